@@ -1,0 +1,50 @@
+"""Host-side input generators: determinism, published PRNG values, config facts."""
+import math
+
+import numpy as np
+
+import workloads as W
+
+
+def test_splitmix64_published_values():
+    # first outputs of SplitMix64 from state 0 (Steele, Lea & Flood 2014 reference code)
+    got = [int(v) for v in W.splitmix64(0, np.arange(3))]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_uniform_range_and_determinism():
+    u = W.uniform01(7, np.arange(100000))
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 0.01
+    assert np.array_equal(u, W.uniform01(7, np.arange(100000)))
+
+
+def test_gaussian_disk_config():
+    p = W.gaussian_disk_32()
+    assert p.rho.shape == (1, 8, 32, 32)
+    assert p.rho.max() == 1e14 * math.exp(-0.5 / 128.0)      # 4 centre cells, r^2 = 0.5
+    assert np.array_equal(p.rho[0, 0], p.rho[0, 7])
+
+
+def test_radial_disk_config():
+    p = W.radial_disk_512()
+    assert p.rho.shape == (2, 16, 512, 512)
+    plane = p.rho[0, 0]
+    assert plane[255, 255] > 1e13 and plane[0, 0] == 0.0
+    assert np.array_equal(p.rho[0], p.rho[1])
+    assert np.allclose(np.linalg.norm(p.t, axis=1), 1.0)
+
+
+def test_gan_polycrystal_small():
+    g = W.Geometry(32, 32, 6, 0.2e-6, 0.2e-6, 0.05e-6)
+    p = W.gan_polycrystal(g, 1e-6, seed=3)
+    assert p.rho.shape == (18, 6, 32, 32)
+    nz_per_cell = (p.rho > 0).sum(axis=0)
+    assert np.all(nz_per_cell == 2)                       # one edge + one mixed family per column
+    edge = (p.rho[:6] > 0).sum(axis=0)
+    assert np.all(edge == 1)
+    prof = W.gan_height_profile(g)
+    assert np.allclose(p.rho.max(axis=(0, 2, 3)), prof)
+    assert p.meta["n_grains"] == round((6.4e-6) ** 2 / (math.pi * 0.25e-12))
+    p2 = W.gan_polycrystal(g, 1e-6, seed=3)
+    assert np.array_equal(p.rho, p2.rho)

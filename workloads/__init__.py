@@ -1,0 +1,265 @@
+"""Seeded synthetic inputs for the dislocation-density stress path.
+
+This module only *generates inputs*: grid geometry, dislocation families
+(line direction t, Burgers vector b) and site-dependent densities rho_f.
+It contains none of the method's arithmetic (no segment stress, no
+interaction coefficients, no FFT), so the FP64 oracle and the GPU path can
+both consume what it produces without sharing any computation.
+
+Units are SI throughout: lengths in metres, moduli in pascal, densities as
+dislocation lines per unit area in m^-2 (the paper quotes cm^-2; 1 cm^-2 =
+1e4 m^-2).  Arrays are C-ordered ``[F][nz][ny][nx]`` (x fastest), cell (i,j,k)
+centred at ((i+1/2)dx, (j+1/2)dy, (k+1/2)dz).
+
+Workload shapes follow the paper's experiments: the disk with a radially /
+vertically varying density of one dislocation type (Sec. 3, Eq. 11, Figs. 4-6)
+and the columnar Voronoi polycrystal with per-grain Burgers vectors drawn from
+the six hexagonal a-type directions, edge and mixed (Sec. 6, Eq. 19).
+
+Random numbers come from the counter-based SplitMix64 generator (Steele,
+Lea & Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014):
+draw i of stream ``seed`` is mix(seed + (i+1) * 0x9E3779B97F4A7C15).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+CM2 = 1.0e4          # 1 cm^-2 in m^-2
+UM = 1.0e-6          # 1 micrometre in m
+NM = 1.0e-9
+
+# Material constants used by every configuration (isotropic, GaN-like).
+MU_GAN = 68.0e9
+NU_GAN = 0.23
+A_LATT = 0.319 * NM   # a-type Burgers length used by the configurations
+C_LATT = 0.519 * NM   # c-type Burgers length
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, index) -> np.ndarray:
+    """SplitMix64 output for draws ``index`` (array-like of ints) of stream ``seed``."""
+    idx = np.asarray(index, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (idx + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, index) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the top 53 bits of SplitMix64."""
+    return (splitmix64(seed, index) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+@dataclass
+class Geometry:
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    dz: float
+    mu: float = MU_GAN
+    nu: float = NU_GAN
+
+    @property
+    def n_cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+@dataclass
+class Problem:
+    """One stress evaluation: geometry, F families and F density fields."""
+    name: str
+    geom: Geometry
+    t: np.ndarray            # (F, 3) unit line directions
+    b: np.ndarray            # (F, 3) Burgers vectors (m)
+    rho: np.ndarray          # (F, nz, ny, nx) float64, m^-2
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_families(self) -> int:
+        return int(self.t.shape[0])
+
+
+def hex_a(i: int, a: float = A_LATT) -> np.ndarray:
+    """In-plane a-type Burgers vector number i (0..5): a (cos 60 i, sin 60 i, 0)."""
+    ang = math.radians(60.0 * i)
+    return np.array([a * math.cos(ang), a * math.sin(ang), 0.0])
+
+
+T_Z = np.array([0.0, 0.0, 1.0])
+
+
+def t_mixed(incline_deg: float = 15.6) -> np.ndarray:
+    """Mixed-dislocation line direction tilted by ``incline_deg`` from z in the y-z plane."""
+    a = math.radians(incline_deg)
+    return np.array([0.0, math.sin(a), math.cos(a)])
+
+
+def cell_centres_xy(geom: Geometry):
+    x = (np.arange(geom.nx) + 0.5) * geom.dx
+    y = (np.arange(geom.ny) + 0.5) * geom.dy
+    return np.meshgrid(x, y, indexing="xy")   # (ny, nx)
+
+
+def cell_centres_z(geom: Geometry) -> np.ndarray:
+    return (np.arange(geom.nz) + 0.5) * geom.dz
+
+
+# ---------------------------------------------------------------------------
+# Configurations
+# ---------------------------------------------------------------------------
+
+def gaussian_disk_32() -> Problem:
+    """32x32x8 grid of 1x1x0.25 um cells, one family of vertical edge dislocations
+    (t = z, b = 0.319 nm along x), density 1e10 cm^-2 * exp(-r^2 / (2 * 8^2)) with r
+    in cells from the grid centre, uniform in z (the Gaussian disk profile of Eq. 11
+    without the z decay)."""
+    g = Geometry(32, 32, 8, 1.0 * UM, 1.0 * UM, 0.25 * UM)
+    i = np.arange(g.nx) - 15.5
+    j = np.arange(g.ny) - 15.5
+    r2 = j[:, None] ** 2 + i[None, :] ** 2
+    plane = 1.0e10 * CM2 * np.exp(-r2 / (2.0 * 8.0 ** 2))
+    rho = np.broadcast_to(plane, (1, g.nz, g.ny, g.nx)).astype(np.float64).copy()
+    return Problem("gaussian_disk_32x32x8", g, T_Z[None, :].copy(),
+                   np.array([[A_LATT, 0.0, 0.0]]), rho)
+
+
+def radial_disk_512() -> Problem:
+    """512x512x16 grid of 0.5x0.5x0.2 um cells; two families carrying the same density
+    rho(r) = 1e9 (1 + 4 (r/R)^2) cm^-2 inside a disk of radius R = 240 cells about the
+    grid centre, zero outside, uniform in z.  Family 1: vertical edge (t = z, b = a x).
+    Family 2: mixed, t = (0, 1/2, sqrt3/2), b = (a/2, sqrt3 a/2, c), the mixed type of
+    the paper's disk example (Sec. 3, Fig. 6)."""
+    g = Geometry(512, 512, 16, 0.5 * UM, 0.5 * UM, 0.2 * UM)
+    i = np.arange(g.nx) - 255.5
+    j = np.arange(g.ny) - 255.5
+    r = np.sqrt(j[:, None] ** 2 + i[None, :] ** 2)
+    R = 240.0
+    plane = np.where(r < R, 1.0e9 * CM2 * (1.0 + 4.0 * (r / R) ** 2), 0.0)
+    rho1 = np.broadcast_to(plane, (g.nz, g.ny, g.nx))
+    rho = np.stack([rho1, rho1]).astype(np.float64)
+    s3 = math.sqrt(3.0)
+    t = np.array([[0.0, 0.0, 1.0], [0.0, 0.5, s3 / 2.0]])
+    b = np.array([[A_LATT, 0.0, 0.0], [A_LATT / 2.0, s3 * A_LATT / 2.0, C_LATT]])
+    return Problem("radial_disk_512x512x16", g, t, b, rho)
+
+
+def gan_families(incline_deg: float = 15.6):
+    """The 18 families of the polycrystalline GaN-like layer: 6 vertical edge
+    dislocations with b = a_i, then 12 mixed ones (tilted t, b = a_i + s c z,
+    s = +1 for even slots, -1 for odd).  Returns (t, b) arrays of shape (18, 3)."""
+    t = []
+    b = []
+    for i in range(6):
+        t.append(T_Z)
+        b.append(hex_a(i))
+    tm = t_mixed(incline_deg)
+    for i in range(6):
+        for s in (1.0, -1.0):
+            t.append(tm)
+            b.append(hex_a(i) + np.array([0.0, 0.0, s * C_LATT]))
+    return np.array(t), np.array(b)
+
+
+def voronoi_columns(geom: Geometry, n_seeds: int, seed: int) -> np.ndarray:
+    """Grain id per column (ny, nx): nearest of ``n_seeds`` seeds drawn uniformly in
+    the layer plane (open boundary), ties to the lower id.  Vertical grain boundaries
+    as in the paper's polycrystal (Sec. 6)."""
+    Lx, Ly = geom.nx * geom.dx, geom.ny * geom.dy
+    u = uniform01(seed, np.arange(2 * n_seeds))
+    sx = Lx * u[0::2]
+    sy = Ly * u[1::2]
+    X, Y = cell_centres_xy(geom)
+    xs = X.ravel()
+    ys = Y.ravel()
+    best = np.zeros(xs.size, dtype=np.int64)
+    bestd = np.full(xs.size, np.inf)
+    for k in range(n_seeds):            # ascending id: strict < keeps the lower id on ties
+        d = (xs - sx[k]) ** 2 + (ys - sy[k]) ** 2
+        m = d < bestd
+        best[m] = k
+        bestd[m] = d[m]
+    return best.reshape(geom.ny, geom.nx)
+
+
+def gan_height_profile(geom: Geometry) -> np.ndarray:
+    """rho(z) = 1e10 exp(-z / 0.5 um) + 1e8 cm^-2 at the cell-centre heights."""
+    z = cell_centres_z(geom)
+    return (1.0e10 * np.exp(-z / (0.5 * UM)) + 1.0e8) * CM2
+
+
+def gan_polycrystal(geom: Geometry, grain_diameter: float, seed: int,
+                    name: str = "gan_polycrystal") -> Problem:
+    """Columnar Voronoi polycrystal with mean grain diameter ``grain_diameter``.
+    Each grain draws one edge family (b = a_i) and one mixed family (b = a_i +- c);
+    both carry the height profile rho(z) in every cell of the grain."""
+    Lx, Ly = geom.nx * geom.dx, geom.ny * geom.dy
+    n_seeds = max(1, int(round(Lx * Ly / (math.pi * (grain_diameter / 2.0) ** 2))))
+    grains = voronoi_columns(geom, n_seeds, seed)
+    u = uniform01(seed, 2 * n_seeds + np.arange(3 * n_seeds))
+    edge_idx = np.minimum((6.0 * u[0::3]).astype(np.int64), 5)
+    mix_idx = np.minimum((6.0 * u[1::3]).astype(np.int64), 5)
+    mix_sign = (u[2::3] >= 0.5).astype(np.int64)         # 0 -> +c, 1 -> -c
+    t, b = gan_families()
+    F = t.shape[0]
+    prof = gan_height_profile(geom)
+    rho = np.zeros((F, geom.nz, geom.ny, geom.nx), dtype=np.float64)
+    fam_edge = edge_idx[grains]                          # (ny, nx)
+    fam_mix = 6 + 2 * mix_idx[grains] + mix_sign[grains]
+    for f in range(F):
+        mask = (fam_edge == f) | (fam_mix == f)
+        if mask.any():
+            rho[f] = prof[:, None, None] * mask[None, :, :]
+    return Problem(name, geom, t, b, rho,
+                   meta={"n_grains": n_seeds, "grain_diameter": grain_diameter, "seed": seed})
+
+
+def gan_layer_256(seed: int = 0) -> Problem:
+    """256x256x128 grid of 0.2x0.2x0.05 um cells, Voronoi grains of mean diameter 2 um,
+    18 families (6 edge + 12 mixed), height profile 1e10 exp(-z/0.5um) + 1e8 cm^-2."""
+    g = Geometry(256, 256, 128, 0.2 * UM, 0.2 * UM, 0.05 * UM)
+    return gan_polycrystal(g, 2.0 * UM, seed, name="gan_layer_256x256x128")
+
+
+SWEEP_GRIDS = [(128, 128, 64), (128, 128, 128), (256, 256, 64), (256, 256, 128)]
+
+
+def sweep_realisation(r: int) -> Problem:
+    """Realisation r of the grain-size sweep: grid drawn uniformly from SWEEP_GRIDS,
+    cells 0.2x0.2x0.05 um, grain diameter log-uniform in [0.5, 8] um, grain seed r."""
+    u = uniform01(1000 + r, np.arange(2))
+    nx, ny, nz = SWEEP_GRIDS[min(int(4 * u[0]), 3)]
+    D = math.exp(math.log(0.5) + (math.log(8.0) - math.log(0.5)) * u[1]) * UM
+    g = Geometry(nx, ny, nz, 0.2 * UM, 0.2 * UM, 0.05 * UM)
+    return gan_polycrystal(g, D, r, name=f"sweep_{r}")
+
+
+def random_problem(geom: Geometry, t: np.ndarray, b: np.ndarray, seed: int,
+                   scale: float = 1.0e10 * CM2) -> Problem:
+    """Uniform random densities in [0, scale) for each family (parity tests)."""
+    t = np.asarray(t, dtype=np.float64).reshape(-1, 3)
+    b = np.asarray(b, dtype=np.float64).reshape(-1, 3)
+    F = t.shape[0]
+    n = F * geom.n_cells
+    rho = (scale * uniform01(seed, np.arange(n))).reshape(F, geom.nz, geom.ny, geom.nx)
+    return Problem(f"random_{seed}", geom, t, b, rho)
+
+
+CONFIGS = {
+    "gaussian_disk_32x32x8": gaussian_disk_32,
+    "radial_disk_512x512x16": radial_disk_512,
+    "gan_layer_256x256x128": gan_layer_256,
+}

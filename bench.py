@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Throughput of the FFT dislocation-density stress evaluation on GB300.
+
+One step = one full evaluation sigma = sum_f G^f * rho_f (Eq. 10) through the
+C ABI (x forward, y forward, fused z + contraction, y inverse, x inverse) on the
+512x512x16 disk of two dislocation families (edge + mixed).  Inputs stay resident
+in HBM; L2 is flushed (256 MB write) before every timed step and each step is
+timed with CUDA events on the launching stream.
+
+  python bench.py [--gpus N --steps K --warmup W]        # this implementation
+  python bench.py --impl reference ...                    # FP64 oracle on host cores
+
+Multi-GPU (torchrun): every rank evaluates its own copy of the workload (replicas,
+no data-path collective); the reported time is the maximum over ranks and the
+value counts the cells of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+import workloads as W  # noqa: E402
+
+METRIC = "stress cells/s"
+UNIT = "cells/s"
+DEFAULT_WORKLOAD = "radial_disk_512x512x16"
+PASS_NAMES = ("x_fwd", "y_fwd", "z_fused", "y_inv", "x_inv")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.CONFIGS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- byte model --
+def pass_bytes(p, q):
+    """Algorithmic HBM bytes of each pass of one evaluation (reads + writes the pass
+    must do in this schedule; kernel spectra stored as FP32 imaginary parts)."""
+    g = p.geom
+    N = g.n_cells
+    fin, fe = p.n_families, q["n_fields"]
+    m1 = q["px"] // 2 + 1
+    ny, nz, py, pz = g.ny, g.nz, q["py"], q["pz"]
+    c8 = 8
+    x_spec = m1 * ny * nz * c8          # one field after the x pass
+    y_spec = m1 * py * nz * c8          # one field after the y pass (rows z < nz)
+    return {
+        "x_fwd": fin * N * 4 + fe * x_spec,
+        "y_fwd": fe * x_spec + fe * y_spec,
+        "z_fused": fe * y_spec + 6 * fe * m1 * py * pz * 4 + 6 * y_spec,
+        "y_inv": 6 * y_spec + 6 * x_spec,
+        "x_inv": 6 * x_spec + 6 * N * 4,
+    }
+
+
+def floor_bytes(p, q):
+    """Strict floor per evaluation: read rho, read the kernel spectra once, write sigma."""
+    g = p.geom
+    m1 = q["px"] // 2 + 1
+    return p.n_families * g.n_cells * 4 + 6 * q["n_fields"] * m1 * q["py"] * q["pz"] * 4 + 6 * g.n_cells * 4
+
+
+def measured_peaks():
+    try:
+        return json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
+    except Exception:
+        return {}
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if current."""
+    f = ROOT / "profiles" / "ncu_traffic.json"
+    try:
+        d = json.loads(f.read_text())
+        e = d[workload][kernel]
+        return float(e["dram_bytes_per_launch"]) if e.get("current", False) else None
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------- CPU baseline --
+def oracle_sample(p, seconds: float, seed: int = 0):
+    """Time the FP64 oracle's direct sum on a bounded sample of target cells."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    oracle.stress_direct(p.geom, p.t, p.b, p.rho, targets=rng.integers(0, p.geom.n_cells, size=1), use_table=False)
+    one = max(time.perf_counter() - t0, 1e-3)
+    n = int(max(1, min(4096, seconds / one)))
+    tg = rng.integers(0, p.geom.n_cells, size=n)
+    t0 = time.perf_counter()
+    oracle.stress_direct(p.geom, p.t, p.b, p.rho, targets=tg, use_table=False)
+    dt = time.perf_counter() - t0
+    return n, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    p = W.CONFIGS[args.workload]()
+    per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        oracle_sample(p, min(per_step, 2.0), seed=1)
+    total_cells, total_s, cores = 0, 0.0, 1
+    for k in range(args.steps):
+        n, dt, cores = oracle_sample(p, per_step, seed=100 + k)
+        total_cells += n
+        total_s += dt
+    v = total_cells / total_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [p.geom.nx, p.geom.ny, p.geom.nz],
+                   "families": p.n_families},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{total_cells} sampled target cells, FP64 direct sum of Eq. 10 over all "
+                                   f"{p.geom.n_cells} source cells x {p.n_families} families"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- our arm --
+def run_ours(args):
+    import torch
+
+    import paper_1804_01830_gb300 as dds
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    p = W.CONFIGS[args.workload]()
+    g = p.geom
+    ctx = dds.context_for(p, device=local)
+    q = ctx.query()
+    rho = torch.from_numpy(p.rho.astype(np.float32)).cuda()
+    sigma = torch.empty((6,) + g.shape, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 0)):
+        ctx.stress(rho, sigma)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    dds.dds_profile_enable(ctx.handle, True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        ev0[k].record(stream)
+        ctx.stress(rho, sigma)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
+    per_pass = dds.dds_profile_read(ctx.handle, K)
+    dds.dds_profile_enable(ctx.handle, False)
+    total_ms = float(step_ms.sum())
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * g.n_cells * K / (total_ms / 1e3)
+
+    # roofline of the dominant kernel, measured over the timed region
+    pb = pass_bytes(p, q)
+    mean_pass = per_pass.mean(axis=0)
+    dom = int(np.argmax(mean_pass))
+    dom_name = PASS_NAMES[dom]
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured"
+    if not peak:
+        peak, peak_src = 6800.0, "fallback"
+    achieved = pb[dom_name] / (mean_pass[dom] * 1e-3) / 1e9
+    step_bytes = sum(pb.values())
+
+    # end to end through the host-buffer entry point, pinned buffers
+    e2e = None
+    if not args.no_e2e:
+        rho_h = torch.from_numpy(p.rho.astype(np.float32)).pin_memory()
+        sig_h = torch.empty((6,) + g.shape, dtype=torch.float32).pin_memory()
+        rh, sh = rho_h.numpy(), sig_h.numpy()
+        for _ in range(2):
+            ctx.stress_host(rh, sh)
+        barrier()
+        torch.cuda.synchronize()
+        ke = max(3, min(K, 20))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            ctx.stress_host(rh, sh)
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * g.n_cells * ke / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(rho_h.numel() * 4), "d2h_bytes_per_step": int(sig_h.numel() * 4),
+               "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, dt, cores = oracle_sample(p, args.cpu_seconds)
+        cpu = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} random target cells of {args.workload}, FP64 direct sum of Eq. 10 over all "
+                         f"{g.n_cells} source cells x {p.n_families} families ({dt:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [g.nx, g.ny, g.nz], "families": p.n_families,
+                   "fields": q["n_fields"], "padded": [q["px"], q["py"], q["pz"]],
+                   "cells_per_step": g.n_cells, "l2": "flushed before every step (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(dom_name, args.workload),
+                     "bytes_per_launch": pb[dom_name], "ms_per_launch": float(mean_pass[dom]),
+                     "peak_source": peak_src},
+        "passes_ms": {n: float(v) for n, v in zip(PASS_NAMES, mean_pass)},
+        "step_roofline": {"bytes_pass_model": step_bytes, "bytes_floor": floor_bytes(p, q),
+                          "frac_pass_model": step_bytes / (total_ms / K * 1e-3) / 1e9 / peak},
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "gpu_launches": K * ctx.launches_per_stress,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

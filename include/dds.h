@@ -1,0 +1,153 @@
+/*
+ * dds.h — C ABI of the GB300 dislocation-density stress library (libdds.so).
+ *
+ * Computes the stress created by site-dependent densities of straight
+ * dislocations on a rectangular grid of (possibly strongly shape-anisotropic)
+ * cells, following Berkov & Gorn, "Dislocation-induced stress in polycrystalline
+ * materials: mesoscopic simulations in the dislocation density formalism":
+ *
+ *   sigma_c(r0) = sum_f sum_i G_c^f(r0 - r_i) rho_f(r_i)              (Eq. 10, Eq. 3b)
+ *
+ * over all cells r_i of the grid (open boundary: the sample is embedded in an
+ * infinite elastic continuum, Sec. 3).  G_c^f is the stress at r0 per unit
+ * density of family f = (line direction t, Burgers vector b) in the cell at r_i:
+ * (cell volume / dl) times the stress of one straight segment of length dl
+ * threading that cell through its centre (Eq. 9b with Eq. 6/7), and for cells
+ * closer than the near-field radius the mean over near-cubic target subcells of
+ * the sum over source subcells (Sec. 2.3).  The sum is evaluated as a
+ * zero-padded FFT convolution (Sec. 2.3, first remark on Eq. 10).
+ *
+ * Conventions (all entry points):
+ *   - SI units: lengths in m, moduli in Pa, densities in dislocation lines per m^2
+ *     (1 cm^-2 = 1e4 m^-2), stress in Pa.
+ *   - Grids are C-ordered [nz][ny][nx], x fastest; cell (i,j,k) is centred at
+ *     ((i+1/2)dx, (j+1/2)dy, (k+1/2)dz).
+ *   - Stress components are ordered xx, yy, zz, xy, xz, yz.
+ *   - The library never aborts and never prints.  Every entry point returns
+ *     DDS_OK (0) or a negative DDS_ERR_* code; dds_last_error() then holds a
+ *     one-line message.  A context is not thread-safe: use one context per host
+ *     thread, and at most one stress evaluation in flight per context.
+ *   - Device pointers are CUDA device memory on the context's device (for
+ *     example torch tensors' data_ptr()); the caller owns them.  The library
+ *     owns everything it allocates and frees it in dds_destroy().
+ */
+#ifndef DDS_H
+#define DDS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dds_ctx dds_ctx;
+
+enum {
+  DDS_OK = 0,
+  DDS_ERR_INVALID_ARG = -1,   /* bad pointer, size, direction or option value      */
+  DDS_ERR_NOT_READY = -2,     /* geometry/families missing or kernels not built   */
+  DDS_ERR_OOM = -3,           /* device allocation failed                          */
+  DDS_ERR_CUDA = -4,          /* a CUDA runtime call or kernel launch failed       */
+  DDS_ERR_TIMEOUT = -5,       /* a bounded device wait gave up                     */
+  DDS_ERR_UNSUPPORTED = -6    /* valid request outside this build's limits         */
+};
+
+/* Density element types accepted by dds_stress. */
+enum { DDS_F32 = 0, DDS_BF16 = 1 };
+
+/* Option keys for dds_set_option. */
+enum {
+  DDS_OPT_NEAR_RADIUS = 1  /* near-field radius in units of the largest cell edge
+                              (Sec. 2.3 "several nearest-neighbour shells"); default 3;
+                              0 disables subdivision.  Invalidates built kernels. */
+};
+
+/* Limits of this build. */
+#define DDS_MAX_NXY 512        /* nx, ny <= 512 (zero-padded FFT sizes <= 1024)      */
+#define DDS_MAX_NZ 256         /* nz <= 256 (zero-padded FFT size <= 512)            */
+#define DDS_MAX_FAMILIES 64    /* families per context                               */
+#define DDS_MAX_FIELDS 12      /* effective fields after collapsing families         */
+
+/* Create a context bound to CUDA device `cuda_device`.  *out receives the handle
+ * (NULL on failure).  Errors: INVALID_ARG (out NULL or no such device), OOM. */
+int dds_create(dds_ctx **out, int cuda_device);
+
+/* Grid shape and cell edges (m), shear modulus mu (Pa) and Poisson ratio nu of the
+ * isotropic medium (Eq. 4: sigma_0 = mu / 4 pi (1 - nu)).  1 <= nx, ny <= DDS_MAX_NXY,
+ * 1 <= nz <= DDS_MAX_NZ,
+ * cell edges > 0, mu > 0, -1 < nu < 0.5.  Invalidates built kernels. */
+int dds_set_geometry(dds_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz,
+                     double mu, double nu);
+
+/* F dislocation families (Eq. 3b): t[3f..3f+2] the line direction (normalised
+ * here; must be non-zero), b[3f..3f+2] the Burgers vector in m.  Host pointers,
+ * copied.  1 <= F <= DDS_MAX_FAMILIES.  Families sharing a line direction are
+ * combined internally through the linearity of the coefficients in b (Sec. 2.1);
+ * more than DDS_MAX_FIELDS combined fields gives UNSUPPORTED.  Invalidates built
+ * kernels. */
+int dds_set_families(dds_ctx *ctx, int F, const double *t, const double *b);
+
+/* Set an option (see DDS_OPT_*).  INVALID_ARG for an unknown key or bad value. */
+int dds_set_option(dds_ctx *ctx, int key, double value);
+
+/* Build the interaction coefficients in FP64 on the device (Eq. 9b, Eq. 6/7,
+ * Sec. 2.3 near field) and their FP32 Fourier spectra, and size the work buffers.
+ * Done once per geometry and family set (Sec. 2.3); later calls with nothing
+ * changed return at once.  Runs on `cuda_stream` (a cudaStream_t, NULL = legacy
+ * default stream) and synchronises it before returning. */
+int dds_build_kernels(dds_ctx *ctx, void *cuda_stream);
+
+/* sigma = sum over families of G * rho (Eq. 10).  rho: device, [F][nz][ny][nx] in
+ * m^-2, element type rho_dtype (DDS_F32; DDS_BF16 stores the density as bfloat16,
+ * arithmetic stays FP32).  sigma: device, [6][nz][ny][nx] float32, Pa.  Both must be
+ * 16-byte aligned.  Enqueued on `cuda_stream`; returns without synchronising.
+ * NOT_READY before dds_build_kernels. */
+int dds_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, void *cuda_stream);
+
+/* As dds_stress for n contexts (each built), inputs rho[i] -> sigma[i], all enqueued
+ * on one stream in order. */
+int dds_stress_batched(dds_ctx **ctxs, int n, const void **rho, const int *rho_dtype,
+                       float **sigma, void *cuda_stream);
+
+/* End-to-end variant with HOST buffers: copies rho_host (float32, [F][nz][ny][nx])
+ * to the device, evaluates, copies sigma back to sigma_host (float32,
+ * [6][nz][ny][nx]) and synchronises the stream.  Device staging buffers are owned
+ * by the context. */
+int dds_stress_host(dds_ctx *ctx, const float *rho_host, float *sigma_host, void *cuda_stream);
+
+/* FP64 interaction coefficients of one family (t, b) under the current geometry
+ * and options, evaluated on the device by the same code that builds the kernels:
+ * out_host[6q..6q+5] = G(i, j, k) for offsets ijk_host[3q..3q+2] (observer cell
+ * minus source cell, |i| < nx, |j| < ny, |k| < nz), q < n.  Host pointers;
+ * synchronous.  For parity tests. */
+int dds_table_at(dds_ctx *ctx, const double t[3], const double b[3], long n,
+                 const int *ijk_host, double *out_host);
+
+/* Sizes: number of effective fields after collapsing families, padded FFT sizes. */
+int dds_query(const dds_ctx *ctx, int *n_fields, int *px, int *py, int *pz);
+
+/* Number of kernel launches one dds_stress call issues. */
+int dds_launches_per_stress(const dds_ctx *ctx);
+
+/* Per-pass timing.  While enabled, every dds_stress on this context records CUDA
+ * events on its stream before the first pass and after each pass (the passes are
+ * x forward, y forward, fused z, y inverse, x inverse).  Timing only; results are
+ * unchanged.  Enabling clears earlier records. */
+int dds_profile_enable(dds_ctx *ctx, int enable);
+
+/* Synchronise the recorded events and return their durations: ms_out (host,
+ * [max_steps][5]) gets per-pass milliseconds of the first min(recorded, max_steps)
+ * evaluations since enabling; *n_steps and *n_passes receive the counts.  Clears
+ * the records. */
+int dds_profile_read(dds_ctx *ctx, int max_steps, float *ms_out, int *n_steps, int *n_passes);
+
+/* Last error message of this context (never NULL; "" if none). */
+const char *dds_last_error(const dds_ctx *ctx);
+
+/* Free everything the context owns.  NULL is a no-op. */
+void dds_destroy(dds_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDS_H */

@@ -1,0 +1,276 @@
+"""GB300 dislocation-density stress: Python binding of ``libdds.so``.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI declared in ``include/dds.h``.  The module-level
+functions carry the C names (``dds_create``, ``dds_set_geometry``, ...);
+``StressContext`` wraps them for convenience.  PyTorch supplies device memory
+and streams.  If the library has not been built this module raises on import of
+any entry point -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libdds.so"
+
+DDS_OK = 0
+DDS_ERR_INVALID_ARG = -1
+DDS_ERR_NOT_READY = -2
+DDS_ERR_OOM = -3
+DDS_ERR_CUDA = -4
+DDS_ERR_TIMEOUT = -5
+DDS_ERR_UNSUPPORTED = -6
+DDS_F32 = 0
+DDS_BF16 = 1
+DDS_OPT_NEAR_RADIUS = 1
+
+# Every symbol include/dds.h declares.
+EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option",
+           "dds_build_kernels", "dds_stress", "dds_stress_batched", "dds_stress_host",
+           "dds_table_at", "dds_query", "dds_launches_per_stress", "dds_profile_enable",
+           "dds_profile_read", "dds_last_error", "dds_destroy")
+
+PASS_NAMES = ("x_fwd", "y_fwd", "z_fused", "y_inv", "x_inv")
+
+_lib = None
+
+
+class DDSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dds error {code}: {msg}")
+        self.code = code
+
+
+def load_library():
+    """Load libdds.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(str(LIB_PATH))
+    vp, dp, ip, lp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_long
+    sig = {
+        "dds_create": ([ctypes.POINTER(vp), ctypes.c_int], ctypes.c_int),
+        "dds_set_geometry": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_double, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+        "dds_set_families": ([vp, ctypes.c_int, dp, dp], ctypes.c_int),
+        "dds_set_option": ([vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
+        "dds_build_kernels": ([vp, vp], ctypes.c_int),
+        "dds_stress": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "dds_stress_batched": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), ip,
+                                ctypes.POINTER(vp), vp], ctypes.c_int),
+        "dds_stress_host": ([vp, vp, vp, vp], ctypes.c_int),
+        "dds_table_at": ([vp, dp, dp, lp, ip, dp], ctypes.c_int),
+        "dds_query": ([vp, ip, ip, ip, ip], ctypes.c_int),
+        "dds_launches_per_stress": ([vp], ctypes.c_int),
+        "dds_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
+        "dds_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ip, ip], ctypes.c_int),
+        "dds_last_error": ([vp], ctypes.c_char_p),
+        "dds_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(ctx, rc: int):
+    if rc != DDS_OK:
+        msg = load_library().dds_last_error(ctx).decode() if ctx else ""
+        raise DDSError(rc, msg)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---- C-named entry points ---------------------------------------------------
+def dds_create(device: int = 0):
+    h = ctypes.c_void_p()
+    _check(None, load_library().dds_create(ctypes.byref(h), int(device)))
+    return h
+
+
+def dds_set_geometry(ctx, nx, ny, nz, dx, dy, dz, mu, nu):
+    _check(ctx, load_library().dds_set_geometry(ctx, int(nx), int(ny), int(nz), float(dx), float(dy),
+                                                float(dz), float(mu), float(nu)))
+
+
+def dds_set_families(ctx, t, b):
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(-1, 3))
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(-1, 3))
+    _check(ctx, load_library().dds_set_families(ctx, t.shape[0], _dptr(t), _dptr(b)))
+
+
+def dds_set_option(ctx, key: int, value: float):
+    _check(ctx, load_library().dds_set_option(ctx, int(key), float(value)))
+
+
+def dds_build_kernels(ctx, stream=None):
+    _check(ctx, load_library().dds_build_kernels(ctx, _stream_handle(stream)))
+
+
+def dds_stress(ctx, rho_ptr: int, rho_dtype: int, sigma_ptr: int, stream=None):
+    _check(ctx, load_library().dds_stress(ctx, ctypes.c_void_p(rho_ptr), int(rho_dtype),
+                                          ctypes.c_void_p(sigma_ptr), _stream_handle(stream)))
+
+
+def dds_stress_batched(ctxs, rho_ptrs, rho_dtypes, sigma_ptrs, stream=None):
+    n = len(ctxs)
+    arr_c = (ctypes.c_void_p * n)(*[c.value for c in ctxs])
+    arr_r = (ctypes.c_void_p * n)(*rho_ptrs)
+    arr_d = (ctypes.c_int * n)(*rho_dtypes)
+    arr_s = (ctypes.c_void_p * n)(*sigma_ptrs)
+    rc = load_library().dds_stress_batched(arr_c, n, arr_r, arr_d, arr_s, _stream_handle(stream))
+    _check(ctxs[0] if n else None, rc)
+
+
+def dds_stress_host(ctx, rho_host: np.ndarray, sigma_host: np.ndarray, stream=None):
+    assert rho_host.dtype == np.float32 and rho_host.flags.c_contiguous
+    assert sigma_host.dtype == np.float32 and sigma_host.flags.c_contiguous
+    _check(ctx, load_library().dds_stress_host(ctx, ctypes.c_void_p(rho_host.ctypes.data),
+                                               ctypes.c_void_p(sigma_host.ctypes.data),
+                                               _stream_handle(stream)))
+
+
+def dds_table_at(ctx, t, b, ijk) -> np.ndarray:
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(3))
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(3))
+    ijk = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1, 3))
+    out = np.zeros((ijk.shape[0], 6))
+    _check(ctx, load_library().dds_table_at(ctx, _dptr(t), _dptr(b), ijk.shape[0],
+                                            ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(out)))
+    return out
+
+
+def dds_query(ctx):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(ctx, load_library().dds_query(ctx, *[ctypes.byref(x) for x in v]))
+    return {"n_fields": v[0].value, "px": v[1].value, "py": v[2].value, "pz": v[3].value}
+
+
+def dds_launches_per_stress(ctx) -> int:
+    return int(load_library().dds_launches_per_stress(ctx))
+
+
+def dds_profile_enable(ctx, enable: bool = True):
+    _check(ctx, load_library().dds_profile_enable(ctx, int(bool(enable))))
+
+
+def dds_profile_read(ctx, max_steps: int) -> np.ndarray:
+    """Per-pass milliseconds of the evaluations recorded since enabling, (steps, 5)."""
+    out = np.zeros((max(int(max_steps), 1), 5), dtype=np.float32)
+    ns, npass = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, load_library().dds_profile_read(ctx, int(max_steps),
+                                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                ctypes.byref(ns), ctypes.byref(npass)))
+    return out[: ns.value, : npass.value]
+
+
+def dds_last_error(ctx) -> str:
+    return load_library().dds_last_error(ctx).decode()
+
+
+def dds_destroy(ctx):
+    if ctx:
+        load_library().dds_destroy(ctx)
+
+
+# ---- convenience wrapper ------------------------------------------------------
+class StressContext:
+    """One geometry + family set with its cached kernel spectra on one GPU."""
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        self.handle = dds_create(self.device)
+        self.shape = None
+        self.n_families = 0
+
+    def close(self):
+        if self.handle:
+            dds_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_geometry(self, nx, ny, nz, dx, dy, dz, mu, nu):
+        dds_set_geometry(self.handle, nx, ny, nz, dx, dy, dz, mu, nu)
+        self.shape = (int(nz), int(ny), int(nx))
+        return self
+
+    def set_families(self, t, b):
+        dds_set_families(self.handle, t, b)
+        self.n_families = int(np.asarray(t).reshape(-1, 3).shape[0])
+        return self
+
+    def set_option(self, key, value):
+        dds_set_option(self.handle, key, value)
+        return self
+
+    def build_kernels(self, stream=None):
+        dds_build_kernels(self.handle, stream)
+        return self
+
+    def stress(self, rho, sigma=None, stream=None):
+        """rho: CUDA tensor (F, nz, ny, nx) float32 or bfloat16 -> sigma (6, nz, ny, nx) float32."""
+        import torch
+        if not rho.is_cuda or not rho.is_contiguous():
+            raise ValueError("rho must be a contiguous CUDA tensor")
+        if tuple(rho.shape) != (self.n_families,) + self.shape:
+            raise ValueError(f"rho has shape {tuple(rho.shape)}, expected {(self.n_families,) + self.shape}")
+        dt = {torch.float32: DDS_F32, torch.bfloat16: DDS_BF16}.get(rho.dtype)
+        if dt is None:
+            raise ValueError(f"unsupported density dtype {rho.dtype}")
+        if sigma is None:
+            sigma = torch.empty((6,) + self.shape, dtype=torch.float32, device=rho.device)
+        dds_stress(self.handle, rho.data_ptr(), dt, sigma.data_ptr(), stream)
+        return sigma
+
+    def stress_host(self, rho_host: np.ndarray, sigma_host: np.ndarray | None = None, stream=None):
+        rho_host = np.ascontiguousarray(rho_host, dtype=np.float32)
+        if sigma_host is None:
+            sigma_host = np.empty((6,) + self.shape, dtype=np.float32)
+        dds_stress_host(self.handle, rho_host, sigma_host, stream)
+        return sigma_host
+
+    def table_at(self, t, b, ijk):
+        return dds_table_at(self.handle, t, b, ijk)
+
+    def query(self):
+        return dds_query(self.handle)
+
+    @property
+    def launches_per_stress(self) -> int:
+        return dds_launches_per_stress(self.handle)
+
+
+def context_for(problem, device: int = 0, n_near: float | None = None, stream=None) -> StressContext:
+    """Context set up and built for a ``workloads.Problem``-like object (geom, t, b)."""
+    g = problem.geom
+    ctx = StressContext(device)
+    ctx.set_geometry(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.mu, g.nu)
+    ctx.set_families(problem.t, problem.b)
+    if n_near is not None:
+        ctx.set_option(DDS_OPT_NEAR_RADIUS, n_near)
+    ctx.build_kernels(stream)
+    return ctx

@@ -1,0 +1,534 @@
+// C ABI of libdds: validation, family collapse, FFT plan, buffers, entry points.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "dds_fft.cuh"
+#include "dds_internal.h"
+
+namespace dds {
+
+int fail(dds_ctx *ctx, int code, const char *fmt, ...) {
+  if (ctx) {
+    char msg[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof(msg), fmt, ap);
+    va_end(ap);
+    ctx->err = msg;
+  }
+  return code;
+}
+
+// Subcells as close to cubic as possible (Sec. 2.3): per axis the integer m >= 1
+// minimising |ln((h/m) / h_min)|; of the two integers around r = h / h_min the
+// larger wins when m_lo * m_hi <= r^2 (ties included).
+void subcell_counts(const double h[3], int m[3]) {
+  const double hmin = std::min(h[0], std::min(h[1], h[2]));
+  for (int a = 0; a < 3; ++a) {
+    const double r = h[a] / hmin;
+    int lo = (int)floor(r);
+    if (lo < 1) lo = 1;
+    const int hi = lo + 1;
+    m[a] = ((double)lo * (double)hi <= r * r) ? hi : lo;
+  }
+}
+
+double chord_length(const double h[3], const double t[3]) {
+  double dl = INFINITY;
+  for (int a = 0; a < 3; ++a)
+    if (t[a] != 0.0) dl = std::min(dl, h[a] / fabs(t[a]));
+  return dl;
+}
+
+// Near field: |(i dx, j dy, k dz)| < n_near * max(h), evaluated as
+// ((x*x + y*y) + z*z) < r*r in IEEE double without contraction.
+bool is_near(const double h[3], double n_near, int i, int j, int k) {
+  const double hmax = std::max(h[0], std::max(h[1], h[2]));
+  const double rn = n_near * hmax;
+  const volatile double x = (double)i * h[0], y = (double)j * h[1], z = (double)k * h[2];
+  const volatile double xx = x * x, yy = y * y, zz = z * z;
+  const volatile double s = xx + yy;
+  const volatile double s2 = s + zz;
+  const volatile double r2 = rn * rn;
+  return s2 < r2;
+}
+
+cudaError_t make_twiddles(Twiddles *tw) {
+  std::vector<float2> f(TW_TOTAL);
+  std::vector<double2> d(TW_TOTAL);
+  for (int P = 16; P <= 2048; P *= 2) {
+    for (int k = 0; k < P; ++k) {
+      const double a = -2.0 * 3.14159265358979323846 * (double)k / (double)P;
+      const double c = cos(a), s = sin(a);
+      d[tw_offset(P) + k] = make_double2(c, s);
+      f[tw_offset(P) + k] = make_float2((float)c, (float)s);
+    }
+  }
+  cudaError_t err = cudaMalloc(&tw->f32, sizeof(float2) * TW_TOTAL);
+  if (err == cudaSuccess) err = cudaMalloc(&tw->f64, sizeof(double2) * TW_TOTAL);
+  if (err == cudaSuccess) err = cudaMemcpy(tw->f32, f.data(), sizeof(float2) * TW_TOTAL, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(tw->f64, d.data(), sizeof(double2) * TW_TOTAL, cudaMemcpyHostToDevice);
+  return err;
+}
+
+void free_twiddles(Twiddles *tw) {
+  cudaFree(tw->f32);
+  cudaFree(tw->f64);
+  tw->f32 = nullptr;
+  tw->f64 = nullptr;
+}
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+void free_buffers(dds_ctx *ctx) {
+  cudaFree(ctx->kspec);
+  cudaFree(ctx->bufA);
+  cudaFree(ctx->bufB);
+  cudaFree(ctx->nyqA);
+  cudaFree(ctx->nyqB);
+  ctx->kspec = nullptr;
+  ctx->bufA = ctx->bufB = ctx->nyqA = ctx->nyqB = nullptr;
+  ctx->kspec_floats = ctx->bufA_n = ctx->bufB_n = ctx->nyqA_n = ctx->nyqB_n = 0;
+}
+
+void invalidate(dds_ctx *ctx) { ctx->built = false; }
+
+// Group families by line direction and choose effective fields per group.
+int collapse(dds_ctx *ctx) {
+  const int F = ctx->F;
+  std::vector<int> group_of(F, -1);
+  std::vector<int> leaders;
+  for (int f = 0; f < F; ++f) {
+    for (size_t g = 0; g < leaders.size(); ++g) {
+      const int l = leaders[g];
+      double dmax = 0.0;
+      for (int a = 0; a < 3; ++a) dmax = std::max(dmax, fabs(ctx->t[3 * f + a] - ctx->t[3 * l + a]));
+      if (dmax <= 1e-12) { group_of[f] = (int)g; break; }
+    }
+    if (group_of[f] < 0) {
+      group_of[f] = (int)leaders.size();
+      leaders.push_back(f);
+    }
+  }
+  if ((int)leaders.size() > MAX_GROUPS)
+    return fail(ctx, DDS_ERR_UNSUPPORTED, "set_families: %d distinct line directions (limit %d)",
+                (int)leaders.size(), MAX_GROUPS);
+  Collapse col;
+  memset(&col, 0, sizeof(col));
+  std::vector<double> ft, fb;
+  int fe = 0, pos = 0;
+  for (size_t g = 0; g < leaders.size(); ++g) {
+    std::vector<int> fams;
+    for (int f = 0; f < F; ++f)
+      if (group_of[f] == (int)g) fams.push_back(f);
+    int axes[3], nax = 0;
+    double bmax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      bool any = false;
+      for (int f : fams) {
+        if (ctx->b[3 * f + a] != 0.0) any = true;
+        bmax = std::max(bmax, fabs(ctx->b[3 * f + a]));
+      }
+      if (any) axes[nax++] = a;
+    }
+    const int k = (int)fams.size();
+    const bool own = k <= nax;                 // each family is its own field
+    const int nd = own ? k : nax;
+    col.e0[g] = fe;
+    col.nd[g] = nd;
+    col.f0[g] = pos;
+    col.nf[g] = k;
+    const double *tl = &ctx->t[3 * leaders[g]];
+    for (int d = 0; d < nd; ++d) {
+      ft.insert(ft.end(), tl, tl + 3);
+      if (own) {
+        fb.insert(fb.end(), &ctx->b[3 * fams[d]], &ctx->b[3 * fams[d]] + 3);
+      } else {
+        double bv[3] = {0, 0, 0};
+        bv[axes[d]] = bmax;
+        fb.insert(fb.end(), bv, bv + 3);
+      }
+    }
+    for (int q = 0; q < k; ++q) {
+      const int f = fams[q];
+      col.fam[pos + q] = f;
+      for (int d = 0; d < 3; ++d) {
+        double c = 0.0;
+        if (d < nd) c = own ? (q == d ? 1.0 : 0.0) : ctx->b[3 * f + axes[d]] / bmax;
+        col.coef[pos + q][d] = (float)c;
+      }
+    }
+    pos += k;
+    fe += nd;
+  }
+  if (fe > DDS_MAX_FIELDS)
+    return fail(ctx, DDS_ERR_UNSUPPORTED, "set_families: %d effective fields (limit %d)", fe, DDS_MAX_FIELDS);
+  col.ngroups = (int)leaders.size();
+  ctx->col = col;
+  ctx->fe = fe;
+  ctx->field_t = ft;
+  ctx->field_b = fb;
+  return DDS_OK;
+}
+
+// Padded sizes and the tile width of the fused z pass.
+int make_plan(dds_ctx *ctx) {
+  Shape sh;
+  sh.nx = ctx->nx;
+  sh.ny = ctx->ny;
+  sh.nz = ctx->nz;
+  sh.M = std::max(32, next_pow2(2 * ctx->nx)) / 2;
+  sh.py = std::max(32, next_pow2(2 * ctx->ny));
+  sh.pz = std::max(16, next_pow2(2 * ctx->nz));
+  sh.fin = ctx->F;
+  sh.fe = ctx->fe;
+  sh.wz = 0;
+  const size_t pref = 110 * 1024, cap = 220 * 1024;
+  for (int pass = 0; pass < 2 && sh.wz == 0; ++pass) {
+    for (int W : {64, 32, 16, 8}) {
+      if (W > sh.M || sh.py % W != 0) continue;
+      if (W * sh.pz > 2048 && W != 8) continue;
+      const size_t smem = sizeof(float2) * (size_t)(std::max(sh.fe, 1) + 1) * sh.pz * W;
+      if (smem <= (pass == 0 ? pref : cap)) { sh.wz = W; break; }
+    }
+  }
+  if (sh.wz == 0)
+    return fail(ctx, DDS_ERR_UNSUPPORTED, "no z-pass tile fits shared memory (fields %d, pz %d)", sh.fe, sh.pz);
+  ctx->shape = sh;
+  return DDS_OK;
+}
+
+int alloc_buffers(dds_ctx *ctx) {
+  const Shape &sh = ctx->shape;
+  const size_t fe = (size_t)std::max(sh.fe, 1);
+  const size_t M = sh.M, ny = sh.ny, nz = sh.nz, py = sh.py, pz = sh.pz;
+  const size_t a = std::max(fe * nz * ny * M, 6 * nz * py * M);
+  const size_t b = std::max(fe * nz * py * M, 6 * nz * ny * M);
+  const size_t na = std::max(fe * ny * nz, 6 * py * nz);
+  const size_t nb = std::max(fe * py * nz, 6 * ny * nz);
+  const size_t tiles = py * (M / sh.wz) + py / sh.wz;
+  const size_t ks = tiles * 6 * fe * pz * sh.wz;
+  free_buffers(ctx);
+  cudaError_t err = cudaMalloc(&ctx->bufA, a * sizeof(float2));
+  if (err == cudaSuccess) err = cudaMalloc(&ctx->bufB, b * sizeof(float2));
+  if (err == cudaSuccess) err = cudaMalloc(&ctx->nyqA, na * sizeof(float2));
+  if (err == cudaSuccess) err = cudaMalloc(&ctx->nyqB, nb * sizeof(float2));
+  if (err == cudaSuccess) err = cudaMalloc(&ctx->kspec, ks * sizeof(float));
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    free_buffers(ctx);
+    return fail(ctx, DDS_ERR_OOM, "build_kernels: cannot allocate %.2f GB of device buffers: %s",
+                ((a + b + na + nb) * 8.0 + ks * 4.0) / 1e9, cudaGetErrorString(err));
+  }
+  ctx->bufA_n = a;
+  ctx->bufB_n = b;
+  ctx->nyqA_n = na;
+  ctx->nyqB_n = nb;
+  ctx->kspec_floats = ks;
+  return DDS_OK;
+}
+
+bool finite3(const double *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+
+}  // namespace
+}  // namespace dds
+
+using namespace dds;
+
+extern "C" {
+
+int dds_create(dds_ctx **out, int cuda_device) {
+  if (!out) return DDS_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || cuda_device < 0 || cuda_device >= n) {
+    cudaGetLastError();
+    return DDS_ERR_INVALID_ARG;
+  }
+  dds_ctx *ctx = new (std::nothrow) dds_ctx();
+  if (!ctx) return DDS_ERR_OOM;
+  ctx->device = cuda_device;
+  DeviceGuard guard(cuda_device);
+  if (make_twiddles(&ctx->tw) != cudaSuccess) {
+    cudaGetLastError();
+    free_twiddles(&ctx->tw);
+    delete ctx;
+    return DDS_ERR_OOM;
+  }
+  *out = ctx;
+  return DDS_OK;
+}
+
+int dds_set_geometry(dds_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz, double mu,
+                     double nu) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (nx < 1 || ny < 1 || nz < 1)
+    return fail(ctx, DDS_ERR_INVALID_ARG, "set_geometry: grid %dx%dx%d must be positive", nx, ny, nz);
+  if (nx > DDS_MAX_NXY || ny > DDS_MAX_NXY || nz > DDS_MAX_NZ)
+    return fail(ctx, DDS_ERR_UNSUPPORTED, "set_geometry: grid %dx%dx%d exceeds %dx%dx%d", nx, ny, nz,
+                DDS_MAX_NXY, DDS_MAX_NXY, DDS_MAX_NZ);
+  if (!(dx > 0 && dy > 0 && dz > 0) || !isfinite(dx) || !isfinite(dy) || !isfinite(dz))
+    return fail(ctx, DDS_ERR_INVALID_ARG, "set_geometry: cell edges must be positive and finite");
+  if (!(mu > 0) || !isfinite(mu) || !(nu > -1.0 && nu < 0.5))
+    return fail(ctx, DDS_ERR_INVALID_ARG, "set_geometry: need mu > 0 and -1 < nu < 0.5");
+  ctx->nx = nx;
+  ctx->ny = ny;
+  ctx->nz = nz;
+  ctx->h[0] = dx;
+  ctx->h[1] = dy;
+  ctx->h[2] = dz;
+  ctx->mu = mu;
+  ctx->nu = nu;
+  ctx->has_geom = true;
+  invalidate(ctx);
+  return DDS_OK;
+}
+
+int dds_set_families(dds_ctx *ctx, int F, const double *t, const double *b) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!t || !b) return fail(ctx, DDS_ERR_INVALID_ARG, "set_families: NULL pointer");
+  if (F < 1 || F > DDS_MAX_FAMILIES)
+    return fail(ctx, DDS_ERR_INVALID_ARG, "set_families: F = %d outside [1, %d]", F, DDS_MAX_FAMILIES);
+  std::vector<double> tv(3 * F), bv(b, b + 3 * F);
+  for (int f = 0; f < F; ++f) {
+    if (!finite3(t + 3 * f) || !finite3(b + 3 * f))
+      return fail(ctx, DDS_ERR_INVALID_ARG, "set_families: family %d has a non-finite vector", f);
+    const double n = sqrt(t[3 * f] * t[3 * f] + t[3 * f + 1] * t[3 * f + 1] + t[3 * f + 2] * t[3 * f + 2]);
+    if (!(n > 0)) return fail(ctx, DDS_ERR_INVALID_ARG, "set_families: family %d has t = 0", f);
+    for (int a = 0; a < 3; ++a) tv[3 * f + a] = (fabs(n - 1.0) <= 1e-15) ? t[3 * f + a] : t[3 * f + a] / n;
+  }
+  const int F_old = ctx->F;
+  std::vector<double> t_old = ctx->t, b_old = ctx->b;
+  ctx->F = F;
+  ctx->t = tv;
+  ctx->b = bv;
+  const int rc = collapse(ctx);
+  if (rc != DDS_OK) {
+    ctx->F = F_old;
+    ctx->t = t_old;
+    ctx->b = b_old;
+    return rc;
+  }
+  ctx->has_fam = true;
+  invalidate(ctx);
+  return DDS_OK;
+}
+
+int dds_set_option(dds_ctx *ctx, int key, double value) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  switch (key) {
+    case DDS_OPT_NEAR_RADIUS:
+      if (!(value >= 0.0) || !isfinite(value))
+        return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: near radius must be >= 0");
+      ctx->n_near = value;
+      invalidate(ctx);
+      return DDS_OK;
+    default:
+      return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: unknown key %d", key);
+  }
+}
+
+int dds_build_kernels(dds_ctx *ctx, void *cuda_stream) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!ctx->has_geom || !ctx->has_fam)
+    return fail(ctx, DDS_ERR_NOT_READY, "build_kernels: set geometry and families first");
+  if (ctx->built) return DDS_OK;
+  DeviceGuard guard(ctx->device);
+  int rc = make_plan(ctx);
+  if (rc != DDS_OK) return rc;
+  rc = alloc_buffers(ctx);
+  if (rc != DDS_OK) return rc;
+  if (ctx->fe > 0) {
+    rc = build_spectra(ctx, (cudaStream_t)cuda_stream);
+    if (rc != DDS_OK) return rc;
+  }
+  ctx->built = true;
+  ctx->err.clear();
+  return DDS_OK;
+}
+
+int dds_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, void *cuda_stream) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!ctx->built) return fail(ctx, DDS_ERR_NOT_READY, "stress: call dds_build_kernels first");
+  if (!rho || !sigma) return fail(ctx, DDS_ERR_INVALID_ARG, "stress: NULL pointer");
+  if (rho_dtype != DDS_F32 && rho_dtype != DDS_BF16)
+    return fail(ctx, DDS_ERR_INVALID_ARG, "stress: unknown density type %d", rho_dtype);
+  if (((uintptr_t)rho & 15) || ((uintptr_t)sigma & 15))
+    return fail(ctx, DDS_ERR_INVALID_ARG, "stress: rho and sigma must be 16-byte aligned");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (ctx->fe == 0) {
+    const cudaError_t err = cudaMemsetAsync(sigma, 0, sizeof(float) * 6 * (size_t)ctx->nx * ctx->ny * ctx->nz, s);
+    return err == cudaSuccess ? DDS_OK : fail(ctx, DDS_ERR_CUDA, "stress: %s", cudaGetErrorString(err));
+  }
+  return enqueue_stress(ctx, rho, rho_dtype, sigma, s);
+}
+
+int dds_stress_batched(dds_ctx **ctxs, int n, const void **rho, const int *rho_dtype, float **sigma,
+                       void *cuda_stream) {
+  if (!ctxs || n < 0 || (n > 0 && (!rho || !sigma))) return DDS_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const int rc = dds_stress(ctxs[i], rho[i], rho_dtype ? rho_dtype[i] : DDS_F32, sigma[i], cuda_stream);
+    if (rc != DDS_OK) return rc;
+  }
+  return DDS_OK;
+}
+
+int dds_stress_host(dds_ctx *ctx, const float *rho_host, float *sigma_host, void *cuda_stream) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!ctx->built) return fail(ctx, DDS_ERR_NOT_READY, "stress_host: call dds_build_kernels first");
+  if (!rho_host || !sigma_host) return fail(ctx, DDS_ERR_INVALID_ARG, "stress_host: NULL pointer");
+  DeviceGuard guard(ctx->device);
+  const size_t N = (size_t)ctx->nx * ctx->ny * ctx->nz;
+  const size_t rb = sizeof(float) * N * ctx->F, sb = sizeof(float) * N * 6;
+  if (ctx->h2d_rho_bytes < rb) {
+    cudaFree(ctx->h2d_rho);
+    ctx->h2d_rho = nullptr;
+    ctx->h2d_rho_bytes = 0;
+    if (cudaMalloc(&ctx->h2d_rho, rb) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, DDS_ERR_OOM, "stress_host: cannot allocate %zu bytes", rb);
+    }
+    ctx->h2d_rho_bytes = rb;
+  }
+  if (ctx->h2d_sigma_bytes < sb) {
+    cudaFree(ctx->h2d_sigma);
+    ctx->h2d_sigma = nullptr;
+    ctx->h2d_sigma_bytes = 0;
+    if (cudaMalloc(&ctx->h2d_sigma, sb) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, DDS_ERR_OOM, "stress_host: cannot allocate %zu bytes", sb);
+    }
+    ctx->h2d_sigma_bytes = sb;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaError_t err = cudaMemcpyAsync(ctx->h2d_rho, rho_host, rb, cudaMemcpyHostToDevice, s);
+  if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress_host: H2D copy: %s", cudaGetErrorString(err));
+  int rc = dds_stress(ctx, ctx->h2d_rho, DDS_F32, ctx->h2d_sigma, cuda_stream);
+  if (rc != DDS_OK) return rc;
+  err = cudaMemcpyAsync(sigma_host, ctx->h2d_sigma, sb, cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress_host: %s", cudaGetErrorString(err));
+  return DDS_OK;
+}
+
+int dds_table_at(dds_ctx *ctx, const double t[3], const double b[3], long n, const int *ijk_host,
+                 double *out_host) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!ctx->has_geom) return fail(ctx, DDS_ERR_NOT_READY, "table_at: set geometry first");
+  if (!t || !b || (n > 0 && (!ijk_host || !out_host)) || n < 0)
+    return fail(ctx, DDS_ERR_INVALID_ARG, "table_at: bad arguments");
+  if (!finite3(t) || !finite3(b)) return fail(ctx, DDS_ERR_INVALID_ARG, "table_at: non-finite t or b");
+  const double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+  if (!(tn > 0)) return fail(ctx, DDS_ERR_INVALID_ARG, "table_at: t = 0");
+  double tu[3];
+  for (int a = 0; a < 3; ++a) tu[a] = (fabs(tn - 1.0) <= 1e-15) ? t[a] : t[a] / tn;
+  if (n == 0) return DDS_OK;
+  std::vector<unsigned char> near(n);
+  for (long q = 0; q < n; ++q) {
+    const int i = ijk_host[3 * q], j = ijk_host[3 * q + 1], k = ijk_host[3 * q + 2];
+    if (abs(i) >= ctx->nx || abs(j) >= ctx->ny || abs(k) >= ctx->nz)
+      return fail(ctx, DDS_ERR_INVALID_ARG, "table_at: offset (%d,%d,%d) outside the grid", i, j, k);
+    near[q] = ctx->n_near > 0.0 && is_near(ctx->h, ctx->n_near, i, j, k);
+  }
+  DeviceGuard guard(ctx->device);
+  int *d_ijk = nullptr;
+  unsigned char *d_near = nullptr;
+  double *d_out = nullptr;
+  cudaError_t err = cudaMalloc(&d_ijk, sizeof(int) * 3 * n);
+  if (err == cudaSuccess) err = cudaMalloc(&d_near, n);
+  if (err == cudaSuccess) err = cudaMalloc(&d_out, sizeof(double) * 6 * n);
+  if (err == cudaSuccess) err = cudaMemcpy(d_ijk, ijk_host, sizeof(int) * 3 * n, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(d_near, near.data(), n, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = launch_table_at(make_coef_geom(ctx), tu, b, n, d_ijk, d_near, d_out, 0);
+  if (err == cudaSuccess) err = cudaMemcpy(out_host, d_out, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost);
+  cudaFree(d_ijk);
+  cudaFree(d_near);
+  cudaFree(d_out);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, DDS_ERR_CUDA, "table_at: %s", cudaGetErrorString(err));
+  }
+  return DDS_OK;
+}
+
+int dds_query(const dds_ctx *ctx, int *n_fields, int *px, int *py, int *pz) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!ctx->built) return DDS_ERR_NOT_READY;
+  if (n_fields) *n_fields = ctx->fe;
+  if (px) *px = 2 * ctx->shape.M;
+  if (py) *py = ctx->shape.py;
+  if (pz) *pz = ctx->shape.pz;
+  return DDS_OK;
+}
+
+int dds_launches_per_stress(const dds_ctx *ctx) {
+  if (!ctx || !ctx->built) return 0;
+  return ctx->fe == 0 ? 0 : stress_launch_count(ctx->shape);
+}
+
+int dds_profile_enable(dds_ctx *ctx, int enable) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  ctx->profiling = enable != 0;
+  ctx->prof_steps = 0;
+  return DDS_OK;
+}
+
+int dds_profile_read(dds_ctx *ctx, int max_steps, float *ms_out, int *n_steps, int *n_passes) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (max_steps < 0 || (max_steps > 0 && !ms_out))
+    return fail(ctx, DDS_ERR_INVALID_ARG, "profile_read: bad arguments");
+  DeviceGuard guard(ctx->device);
+  const int steps = std::min(max_steps, ctx->prof_steps);
+  for (int st = 0; st < steps; ++st) {
+    cudaEvent_t *ev = &ctx->prof_events[6 * (size_t)st];
+    cudaError_t err = cudaEventSynchronize(ev[5]);
+    for (int p = 0; p < 5 && err == cudaSuccess; ++p) err = cudaEventElapsedTime(&ms_out[5 * st + p], ev[p], ev[p + 1]);
+    if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "profile_read: %s", cudaGetErrorString(err));
+  }
+  if (n_steps) *n_steps = steps;
+  if (n_passes) *n_passes = 5;
+  ctx->prof_steps = 0;
+  return DDS_OK;
+}
+
+const char *dds_last_error(const dds_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void dds_destroy(dds_ctx *ctx) {
+  if (!ctx) return;
+  {
+    DeviceGuard guard(ctx->device);
+    free_buffers(ctx);
+    free_twiddles(&ctx->tw);
+    cudaFree(ctx->h2d_rho);
+    cudaFree(ctx->h2d_sigma);
+    for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
+  }
+  delete ctx;
+}
+
+}  // extern "C"

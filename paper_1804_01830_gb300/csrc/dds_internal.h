@@ -1,0 +1,114 @@
+// Internal declarations shared by the translation units of libdds.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dds.h"
+
+namespace dds {
+
+constexpr int MAX_GROUPS = 8;
+
+// Families collapsed by line direction (the coefficients are linear in b):
+// group g owns effective fields [e0, e0 + nd) and families fam[f0 .. f0 + nf);
+// field e0 + d receives coef[f0 + q][d] * rho_{fam[f0 + q]}.
+struct Collapse {
+  int ngroups;
+  int e0[MAX_GROUPS], nd[MAX_GROUPS], f0[MAX_GROUPS], nf[MAX_GROUPS];
+  int fam[DDS_MAX_FAMILIES];
+  float coef[DDS_MAX_FAMILIES][3];
+};
+
+// Geometry of one evaluation as the device kernels see it.
+struct Shape {
+  int nx, ny, nz;     // grid
+  int M;              // px / 2 (complex length of the x transform)
+  int py, pz;         // padded y and z sizes
+  int fin, fe;        // input families, effective fields
+  int wz;             // columns per tile of the fused z pass
+};
+
+// FP64 description of a box coefficient (Eq. 9b times the cell volume).
+struct CoefGeom {
+  double h[3];        // cell edges
+  double hs[3];       // subcell edges
+  int m[3];           // subcells per axis
+  double mu, nu;
+};
+
+// Twiddle tables exp(-2 pi i k / P) for P = 16 .. 2048 (see dds_fft.cuh).
+struct Twiddles {
+  float2 *f32 = nullptr;
+  double2 *f64 = nullptr;
+};
+
+}  // namespace dds
+
+struct dds_ctx {
+  int device = 0;
+  // geometry
+  bool has_geom = false;
+  int nx = 0, ny = 0, nz = 0;
+  double h[3] = {0, 0, 0};
+  double mu = 0, nu = 0;
+  double n_near = 3.0;
+  // families
+  bool has_fam = false;
+  int F = 0;
+  std::vector<double> t, b;             // F x 3 each (t normalised)
+  // collapse
+  int fe = 0;
+  std::vector<double> field_t, field_b;  // fe x 3 each
+  dds::Collapse col{};
+  // plan
+  dds::Shape shape{};
+  bool built = false;
+  // device memory
+  dds::Twiddles tw;
+  float *kspec = nullptr;               // [tile][6][fe][pz][wz]
+  size_t kspec_floats = 0;
+  float2 *bufA = nullptr, *bufB = nullptr;        // main work buffers
+  float2 *nyqA = nullptr, *nyqB = nullptr;        // Nyquist-column buffers
+  size_t bufA_n = 0, bufB_n = 0, nyqA_n = 0, nyqB_n = 0;
+  void *h2d_rho = nullptr;              // staging for dds_stress_host
+  float *h2d_sigma = nullptr;
+  size_t h2d_rho_bytes = 0, h2d_sigma_bytes = 0;
+  // per-pass profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_events;   // 6 per recorded evaluation
+  int prof_steps = 0;
+  std::string err;
+};
+
+namespace dds {
+
+// Twiddle tables, created once per context.
+cudaError_t make_twiddles(Twiddles *tw);
+void free_twiddles(Twiddles *tw);
+
+// Subcell rule and chord (host side).
+void subcell_counts(const double h[3], int m[3]);
+double chord_length(const double h[3], const double t[3]);
+bool is_near(const double h[3], double n_near, int i, int j, int k);
+
+// FP64 coefficients at a list of offsets (device arrays), near flags per offset.
+cudaError_t launch_table_at(const CoefGeom &g, const double t[3], const double b[3], long n,
+                            const int *d_ijk, const unsigned char *d_near, double *d_out,
+                            cudaStream_t s);
+
+CoefGeom make_coef_geom(const dds_ctx *ctx);
+
+// Build the FP32 kernel spectra of all effective fields into ctx->kspec.
+int build_spectra(dds_ctx *ctx, cudaStream_t s);
+
+// Enqueue one stress evaluation.
+int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s);
+int stress_launch_count(const Shape &sh);
+
+// Set ctx->err (printf-style) and return code.
+int fail(dds_ctx *ctx, int code, const char *fmt, ...);
+
+}  // namespace dds

@@ -1,0 +1,489 @@
+// FP32 evaluation of sigma_c = sum_e G_c^e * rho_e (Eq. 10) as a zero-padded FFT
+// convolution (Sec. 2.3, first remark), in five passes over HBM:
+//
+//   x_fwd : densities of the F input families -> effective fields (linear in b),
+//           real-to-complex FFT along x of the non-zero half of each padded line
+//           (2M points, of which the last M are zero and never read);
+//   y_fwd : FFT along y, input rows y < ny, output all py rows;
+//   z     : per tile of (kx, ky) columns: FFT along z of every field (input rows
+//           z < nz), contraction with the cached kernel spectra
+//             sigma^_c(k) = sum_e (i g_ce(k)) rho^_e(k)      (g = Im G^ / P, G odd),
+//           inverse FFT along z, keep rows z < nz;
+//   y_inv : inverse FFT along y, keep rows y < ny;
+//   x_inv : complex-to-real inverse FFT along x, keep x < nx.
+//
+// The Nyquist column kx = M of the half spectrum travels in separate small
+// arrays.  Layouts (complex):
+//   after x_fwd : main [e][z][y][kx < M],  nyq [e][y][z]
+//   after y_fwd : main [e][z][ky][kx],     nyq [e][ky][z]
+//   after z     : main [c][z][ky][kx],     nyq [c][ky][z]
+//   after y_inv : main [c][z][y][kx],      nyq [c][y][z]
+// Every tile keeps its lines interleaved in shared memory (lanes across lines),
+// so global accesses are contiguous rows of W complex values.
+#include "dds_fft.cuh"
+#include "dds_internal.h"
+
+namespace dds {
+
+namespace {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ float2 cmadd_i(float2 acc, float g, float2 r) {
+  // acc + (i g) * r
+  return make_float2(fmaf(-g, r.y, acc.x), fmaf(g, r.x, acc.y));
+}
+
+__device__ __forceinline__ float bf16_to_f32(uint16_t v) { return __uint_as_float(((uint32_t)v) << 16); }
+
+// ---------------------------------------------------------------- x forward --
+template <int M, bool BF16>
+__global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, const void *rho_v, float2 *out_main,
+                                              float2 *out_nyq, const float2 *tw) {
+  constexpr int W = 16, LD = W + 1;
+  constexpr int OWN = (W * (M / 2) + NT - 1) / NT;
+  extern __shared__ float2 smem[];
+  float2 *buf = smem;
+  const int tid = threadIdx.x;
+  const long L = (long)sh.ny * sh.nz;
+  const long N = L * sh.nx;
+  const long l0 = (long)blockIdx.x * W;
+  const int g = blockIdx.y;
+  const int nxh = (sh.nx + 1) >> 1;
+  const bool even = (sh.nx & 1) == 0;
+  const float2 *twM = tw + tw_offset(M);
+  const float2 *tw2 = tw + tw_offset(2 * M);
+
+  for (int d = 0; d < col.nd[g]; ++d) {
+    float2 acc[OWN];
+#pragma unroll
+    for (int i = 0; i < OWN; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int q = 0; q < col.nf[g]; ++q) {
+      const float cf = col.coef[col.f0[g] + q][d];
+      if (cf == 0.f) continue;
+      const long fbase = (long)col.fam[col.f0[g] + q] * N + l0 * sh.nx;
+#pragma unroll
+      for (int i = 0; i < OWN; ++i) {
+        const int p = tid + i * NT;
+        if (p < W * nxh) {
+          const int w = p / nxh, n = p - w * nxh;
+          if (l0 + w < L) {
+            const long o = fbase + (long)w * sh.nx + 2 * n;
+            float2 v;
+            if (BF16) {
+              const uint16_t *r = (const uint16_t *)rho_v;
+              v.x = bf16_to_f32(r[o]);
+              v.y = (2 * n + 1 < sh.nx) ? bf16_to_f32(r[o + 1]) : 0.f;
+            } else {
+              const float *r = (const float *)rho_v;
+              if (even) {
+                v = *reinterpret_cast<const float2 *>(r + o);
+              } else {
+                v.x = r[o];
+                v.y = (2 * n + 1 < sh.nx) ? r[o + 1] : 0.f;
+              }
+            }
+            acc[i].x = fmaf(cf, v.x, acc[i].x);
+            acc[i].y = fmaf(cf, v.y, acc[i].y);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < OWN; ++i) {
+      const int p = tid + i * NT;
+      if (p < W * nxh) {
+        const int w = p / nxh, n = p - w * nxh;
+        buf[n * LD + w] = acc[i];
+      }
+    }
+    for (int p = W * nxh + tid; p < W * (M / 2); p += NT) {   // zero the tail of the non-zero half
+      const int w = p % W, n = p / W;
+      buf[n * LD + w] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft_tile<M, W, LD, NT, false, true, false>(buf, twM, tid);
+    const int e = col.e0[g] + d;
+    for (int p = tid; p < W * M; p += NT) {
+      const int w = p / M, k = p - w * M;
+      const long line = l0 + w;
+      if (line >= L) continue;
+      const float2 a = buf[k * LD + w];
+      const float2 c = buf[((M - k) & (M - 1)) * LD + w];
+      const float2 E = make_float2(0.5f * (a.x + c.x), 0.5f * (a.y - c.y));
+      const float2 O = make_float2(0.5f * (a.y + c.y), -0.5f * (a.x - c.x));
+      const float2 wk = __ldg(tw2 + k);
+      float2 X;
+      X.x = E.x + (wk.x * O.x - wk.y * O.y);
+      X.y = E.y + (wk.x * O.y + wk.y * O.x);
+      out_main[((long)e * L + line) * M + k] = X;
+      if (k == 0) {
+        const int z = (int)(line / sh.ny), y = (int)(line - (long)z * sh.ny);
+        out_nyq[((long)e * sh.ny + y) * sh.nz + z] = make_float2(E.x - O.x, E.y - O.y);   // W^M = -1
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- y passes -----
+// Forward: rows y < ny in, all py rows out.  Inverse: all py rows in, y < ny out.
+template <int PY, int W, bool INV>
+__global__ void __launch_bounds__(NT) k_ypass(Shape sh, int nf, const float2 *in_main, const float2 *in_nyq,
+                                              float2 *out_main, float2 *out_nyq, const float2 *tw) {
+  constexpr int LD = W;
+  extern __shared__ float2 smem[];
+  float2 *buf = smem;
+  const int tid = threadIdx.x;
+  const int M = sh.M, nz = sh.nz;
+  const int rows_in = INV ? PY : sh.ny;
+  const int rows_out = INV ? sh.ny : PY;
+  const long ktiles = M / W;
+  const long tiles_main = (long)nf * nz * ktiles;
+  const long tau = blockIdx.x;
+  const float2 *in;
+  float2 *out;
+  long rs;
+  int ncols;
+  if (tau < tiles_main) {
+    const int e = (int)(tau / (nz * ktiles));
+    const long r = tau - (long)e * nz * ktiles;
+    const int z = (int)(r / ktiles), kt = (int)(r - (long)z * ktiles);
+    in = in_main + ((long)(e * nz + z) * rows_in) * M + kt * W;
+    out = out_main + ((long)(e * nz + z) * rows_out) * M + kt * W;
+    rs = M;
+    ncols = W;
+  } else {
+    const long t2 = tau - tiles_main;
+    const int ztiles = (nz + W - 1) / W;
+    const int e = (int)(t2 / ztiles), zt = (int)(t2 - (long)e * ztiles);
+    in = in_nyq + (long)e * rows_in * nz + zt * W;
+    out = out_nyq + (long)e * rows_out * nz + zt * W;
+    rs = nz;
+    ncols = min(W, nz - zt * W);
+  }
+  for (int p = tid; p < rows_in * W; p += NT) {
+    const int n = p / W, w = p - n * W;
+    buf[n * LD + w] = (w < ncols) ? in[n * rs + w] : make_float2(0.f, 0.f);
+  }
+  if (!INV) {
+    for (int p = rows_in * W + tid; p < (PY / 2) * W; p += NT) buf[p] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_tile<PY, W, LD, NT, INV, !INV, INV>(buf, tw + tw_offset(PY), tid);
+  for (int p = tid; p < rows_out * W; p += NT) {
+    const int n = p / W, w = p - n * W;
+    if (w < ncols) out[n * rs + w] = buf[n * LD + w];
+  }
+}
+
+// ------------------------------------------------------------- fused z ------
+template <int PZ, int W>
+__global__ void __launch_bounds__(NT) k_zpass(Shape sh, const float2 *in_main, const float2 *in_nyq,
+                                              const float *kspec, float2 *out_main, float2 *out_nyq,
+                                              const float2 *tw) {
+  constexpr int LD = W, TS = PZ * W;
+  extern __shared__ float2 smem[];
+  const int tid = threadIdx.x;
+  const int M = sh.M, py = sh.py, nz = sh.nz, fe = sh.fe;
+  float2 *fields = smem;            // [fe][PZ][W]
+  float2 *obuf = smem + (long)fe * TS;
+  const long ktiles = M / W;
+  const long tiles_main = (long)py * ktiles;
+  const long tau = blockIdx.x;
+  const bool nyq = tau >= tiles_main;
+  long ky = 0, kx0 = 0, ky0 = 0;
+  if (!nyq) {
+    ky = tau / ktiles;
+    kx0 = (tau - ky * ktiles) * W;
+  } else {
+    ky0 = (tau - tiles_main) * W;
+  }
+  // load rows z < nz of every field; zero rows [nz, PZ/2)
+  for (int e = 0; e < fe; ++e) {
+    float2 *f = fields + (long)e * TS;
+    if (!nyq) {
+      const float2 *src = in_main + ((long)e * nz * py + ky) * M + kx0;
+      for (int p = tid; p < nz * W; p += NT) {
+        const int z = p / W, w = p - z * W;
+        f[z * LD + w] = src[(long)z * py * M + w];
+      }
+    } else {
+      const float2 *src = in_nyq + ((long)e * py + ky0) * nz;
+      for (int p = tid; p < nz * W; p += NT) {
+        const int w = p / nz, z = p - w * nz;
+        f[z * LD + w] = src[(long)w * nz + z];
+      }
+    }
+    for (int p = nz * W + tid; p < (PZ / 2) * W; p += NT) f[p] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const float2 *twP = tw + tw_offset(PZ);
+  for (int e = 0; e < fe; ++e) fft_tile<PZ, W, LD, NT, false, true, false>(fields + (long)e * TS, twP, tid);
+
+  const float *ks = kspec + tau * 6L * fe * TS;
+  for (int c = 0; c < 6; ++c) {
+    for (int p = tid; p < TS; p += NT) {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int e = 0; e < fe; ++e) acc = cmadd_i(acc, __ldg(ks + ((long)c * fe + e) * TS + p), fields[(long)e * TS + p]);
+      obuf[p] = acc;
+    }
+    __syncthreads();
+    fft_tile<PZ, W, LD, NT, true, false, true>(obuf, twP, tid);
+    if (!nyq) {
+      float2 *dst = out_main + ((long)c * nz * py + ky) * M + kx0;
+      for (int p = tid; p < nz * W; p += NT) {
+        const int z = p / W, w = p - z * W;
+        dst[(long)z * py * M + w] = obuf[z * LD + w];
+      }
+    } else {
+      float2 *dst = out_nyq + ((long)c * py + ky0) * nz;
+      for (int p = tid; p < nz * W; p += NT) {
+        const int w = p / nz, z = p - w * nz;
+        dst[(long)w * nz + z] = obuf[z * LD + w];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- x inverse --
+template <int M>
+__global__ void __launch_bounds__(NT) k_x_inv(Shape sh, const float2 *in_main, const float2 *in_nyq,
+                                              float *sigma, const float2 *tw) {
+  constexpr int W = 16, LD = W + 1;
+  extern __shared__ float2 smem[];
+  float2 *buf = smem;
+  float2 *xm = smem + M * LD;
+  const int tid = threadIdx.x;
+  const long L = 6L * sh.nz * sh.ny;
+  const long l0 = (long)blockIdx.x * W;
+  for (int p = tid; p < W * M; p += NT) {
+    const int w = p / M, k = p - w * M;
+    buf[k * LD + w] = (l0 + w < L) ? in_main[(l0 + w) * M + k] : make_float2(0.f, 0.f);
+  }
+  if (tid < W) {
+    const long line = l0 + tid;
+    float2 v = make_float2(0.f, 0.f);
+    if (line < L) {
+      const long cz = line / sh.ny;
+      const int y = (int)(line - cz * sh.ny);
+      const int c = (int)(cz / sh.nz), z = (int)(cz - (long)c * sh.nz);
+      v = in_nyq[((long)c * sh.ny + y) * sh.nz + z];
+    }
+    xm[tid] = v;
+  }
+  __syncthreads();
+  // Z[k] = (X[k] + conj X[M-k]) + i W^-k (X[k] - conj X[M-k]); pairs (k, M-k) per thread
+  const float2 *tw2 = tw + tw_offset(2 * M);
+  for (int p = tid; p < W * (M / 2 + 1); p += NT) {
+    const int w = p % W, k = p / W;
+    const float2 A = buf[k * LD + w];
+    const float2 Bm = (k == 0) ? xm[w] : buf[(M - k) * LD + w];   // X[M-k]
+    {
+      const float2 E = make_float2(A.x + Bm.x, A.y - Bm.y);
+      const float2 D = make_float2(A.x - Bm.x, A.y + Bm.y);
+      const float2 wk = __ldg(tw2 + k);                                  // W^k; use conj
+      const float2 O = make_float2(D.x * wk.x + D.y * wk.y, D.y * wk.x - D.x * wk.y);
+      buf[k * LD + w] = make_float2(E.x - O.y, E.y + O.x);
+    }
+    if (k > 0 && k < M / 2) {
+      const float2 E = make_float2(Bm.x + A.x, Bm.y - A.y);
+      const float2 D = make_float2(Bm.x - A.x, Bm.y + A.y);
+      const float2 wk = __ldg(tw2 + (M - k));
+      const float2 O = make_float2(D.x * wk.x + D.y * wk.y, D.y * wk.x - D.x * wk.y);
+      buf[(M - k) * LD + w] = make_float2(E.x - O.y, E.y + O.x);
+    }
+  }
+  __syncthreads();
+  fft_tile<M, W, LD, NT, true, false, true>(buf, tw + tw_offset(M), tid);
+  const int nxh = (sh.nx + 1) >> 1;
+  const bool even = (sh.nx & 1) == 0;
+  for (int p = tid; p < W * nxh; p += NT) {
+    const int w = p / nxh, n = p - w * nxh;
+    const long line = l0 + w;
+    if (line >= L) continue;
+    const float2 v = buf[n * LD + w];
+    float *dst = sigma + line * sh.nx + 2 * n;
+    if (even) {
+      *reinterpret_cast<float2 *>(dst) = v;
+    } else {
+      dst[0] = v.x;
+      if (2 * n + 1 < sh.nx) dst[1] = v.y;
+    }
+  }
+}
+
+// ------------------------------------------------------------ dispatch ------
+template <typename K>
+cudaError_t prep(K kernel, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int y_width(int py) { return py >= 1024 ? 8 : 16; }
+
+template <int M>
+cudaError_t launch_x_fwd(const Shape &sh, const Collapse &col, const void *rho, bool bf16, float2 *om,
+                         float2 *on, const float2 *tw, cudaStream_t s) {
+  const size_t smem = sizeof(float2) * M * 17;
+  const long L = (long)sh.ny * sh.nz;
+  dim3 grid((unsigned)((L + 15) / 16), col.ngroups);
+  cudaError_t err;
+  if (bf16) {
+    if ((err = prep(k_x_fwd<M, true>, smem)) != cudaSuccess) return err;
+    k_x_fwd<M, true><<<grid, NT, smem, s>>>(sh, col, rho, om, on, tw);
+  } else {
+    if ((err = prep(k_x_fwd<M, false>, smem)) != cudaSuccess) return err;
+    k_x_fwd<M, false><<<grid, NT, smem, s>>>(sh, col, rho, om, on, tw);
+  }
+  return cudaGetLastError();
+}
+
+template <int PY, bool INV>
+cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in, float2 *om, float2 *on,
+                     const float2 *tw, cudaStream_t s) {
+  constexpr int W = PY >= 1024 ? 8 : 16;
+  const size_t smem = sizeof(float2) * PY * W;
+  const long tiles = (long)nf * sh.nz * (sh.M / W) + (long)nf * ((sh.nz + W - 1) / W);
+  cudaError_t err = prep(k_ypass<PY, W, INV>, smem);
+  if (err != cudaSuccess) return err;
+  k_ypass<PY, W, INV><<<(unsigned)tiles, NT, smem, s>>>(sh, nf, im, in, om, on, tw);
+  return cudaGetLastError();
+}
+
+template <int PZ, int W>
+cudaError_t launch_z(const Shape &sh, const float2 *im, const float2 *in, const float *ks, float2 *om,
+                     float2 *on, const float2 *tw, cudaStream_t s) {
+  const size_t smem = sizeof(float2) * (size_t)(sh.fe + 1) * PZ * W;
+  const long tiles = (long)sh.py * (sh.M / W) + sh.py / W;
+  cudaError_t err = prep(k_zpass<PZ, W>, smem);
+  if (err != cudaSuccess) return err;
+  k_zpass<PZ, W><<<(unsigned)tiles, NT, smem, s>>>(sh, im, in, ks, om, on, tw);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_x_inv(const Shape &sh, const float2 *im, const float2 *in, float *sigma, const float2 *tw,
+                         cudaStream_t s) {
+  const size_t smem = sizeof(float2) * (M * 17 + 16);
+  const long L = 6L * sh.nz * sh.ny;
+  cudaError_t err = prep(k_x_inv<M>, smem);
+  if (err != cudaSuccess) return err;
+  k_x_inv<M><<<(unsigned)((L + 15) / 16), NT, smem, s>>>(sh, im, in, sigma, tw);
+  return cudaGetLastError();
+}
+
+cudaError_t dispatch_x_fwd(const Shape &sh, const Collapse &col, const void *rho, bool bf16, float2 *om,
+                           float2 *on, const float2 *tw, cudaStream_t s) {
+  switch (sh.M) {
+    case 16: return launch_x_fwd<16>(sh, col, rho, bf16, om, on, tw, s);
+    case 32: return launch_x_fwd<32>(sh, col, rho, bf16, om, on, tw, s);
+    case 64: return launch_x_fwd<64>(sh, col, rho, bf16, om, on, tw, s);
+    case 128: return launch_x_fwd<128>(sh, col, rho, bf16, om, on, tw, s);
+    case 256: return launch_x_fwd<256>(sh, col, rho, bf16, om, on, tw, s);
+    case 512: return launch_x_fwd<512>(sh, col, rho, bf16, om, on, tw, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <bool INV>
+cudaError_t dispatch_y(const Shape &sh, int nf, const float2 *im, const float2 *in, float2 *om, float2 *on,
+                       const float2 *tw, cudaStream_t s) {
+  switch (sh.py) {
+    case 32: return launch_y<32, INV>(sh, nf, im, in, om, on, tw, s);
+    case 64: return launch_y<64, INV>(sh, nf, im, in, om, on, tw, s);
+    case 128: return launch_y<128, INV>(sh, nf, im, in, om, on, tw, s);
+    case 256: return launch_y<256, INV>(sh, nf, im, in, om, on, tw, s);
+    case 512: return launch_y<512, INV>(sh, nf, im, in, om, on, tw, s);
+    case 1024: return launch_y<1024, INV>(sh, nf, im, in, om, on, tw, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Tile widths the planner can choose: W * PZ <= 2048, or W = 8.
+template <int PZ, int W>
+cudaError_t launch_z_if(const Shape &sh, const float2 *im, const float2 *in, const float *ks, float2 *om,
+                        float2 *on, const float2 *tw, cudaStream_t s) {
+  if constexpr (W * PZ <= 2048 || W == 8) return launch_z<PZ, W>(sh, im, in, ks, om, on, tw, s);
+  return cudaErrorInvalidValue;
+}
+
+template <int PZ>
+cudaError_t dispatch_z_w(const Shape &sh, const float2 *im, const float2 *in, const float *ks, float2 *om,
+                         float2 *on, const float2 *tw, cudaStream_t s) {
+  switch (sh.wz) {
+    case 8: return launch_z_if<PZ, 8>(sh, im, in, ks, om, on, tw, s);
+    case 16: return launch_z_if<PZ, 16>(sh, im, in, ks, om, on, tw, s);
+    case 32: return launch_z_if<PZ, 32>(sh, im, in, ks, om, on, tw, s);
+    case 64: return launch_z_if<PZ, 64>(sh, im, in, ks, om, on, tw, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t dispatch_z(const Shape &sh, const float2 *im, const float2 *in, const float *ks, float2 *om,
+                       float2 *on, const float2 *tw, cudaStream_t s) {
+  switch (sh.pz) {
+    case 16: return dispatch_z_w<16>(sh, im, in, ks, om, on, tw, s);
+    case 32: return dispatch_z_w<32>(sh, im, in, ks, om, on, tw, s);
+    case 64: return dispatch_z_w<64>(sh, im, in, ks, om, on, tw, s);
+    case 128: return dispatch_z_w<128>(sh, im, in, ks, om, on, tw, s);
+    case 256: return dispatch_z_w<256>(sh, im, in, ks, om, on, tw, s);
+    case 512: return dispatch_z_w<512>(sh, im, in, ks, om, on, tw, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t dispatch_x_inv(const Shape &sh, const float2 *im, const float2 *in, float *sigma, const float2 *tw,
+                           cudaStream_t s) {
+  switch (sh.M) {
+    case 16: return launch_x_inv<16>(sh, im, in, sigma, tw, s);
+    case 32: return launch_x_inv<32>(sh, im, in, sigma, tw, s);
+    case 64: return launch_x_inv<64>(sh, im, in, sigma, tw, s);
+    case 128: return launch_x_inv<128>(sh, im, in, sigma, tw, s);
+    case 256: return launch_x_inv<256>(sh, im, in, sigma, tw, s);
+    case 512: return launch_x_inv<512>(sh, im, in, sigma, tw, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+int stress_launch_count(const Shape &) { return 5; }
+
+int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s) {
+  const Shape &sh = ctx->shape;
+  const float2 *tw = ctx->tw.f32;
+  cudaEvent_t *ev = nullptr;
+  cudaError_t err = cudaSuccess;
+  if (ctx->profiling) {
+    const size_t need = 6 * (size_t)(ctx->prof_steps + 1);
+    while (err == cudaSuccess && ctx->prof_events.size() < need) {
+      cudaEvent_t e;
+      err = cudaEventCreate(&e);
+      if (err == cudaSuccess) ctx->prof_events.push_back(e);
+    }
+    if (err == cudaSuccess) {
+      ev = &ctx->prof_events[6 * (size_t)ctx->prof_steps];
+      ctx->prof_steps++;
+      err = cudaEventRecord(ev[0], s);
+    }
+  }
+  auto mark = [&](int i) {
+    if (ev && err == cudaSuccess) err = cudaEventRecord(ev[i], s);
+  };
+  if (err == cudaSuccess) err = dispatch_x_fwd(sh, ctx->col, rho, rho_dtype == DDS_BF16, ctx->bufA, ctx->nyqA, tw, s);
+  mark(1);
+  if (err == cudaSuccess) err = dispatch_y<false>(sh, sh.fe, ctx->bufA, ctx->nyqA, ctx->bufB, ctx->nyqB, tw, s);
+  mark(2);
+  if (err == cudaSuccess) err = dispatch_z(sh, ctx->bufB, ctx->nyqB, ctx->kspec, ctx->bufA, ctx->nyqA, tw, s);
+  mark(3);
+  if (err == cudaSuccess) err = dispatch_y<true>(sh, 6, ctx->bufA, ctx->nyqA, ctx->bufB, ctx->nyqB, tw, s);
+  mark(4);
+  if (err == cudaSuccess) err = dispatch_x_inv(sh, ctx->bufB, ctx->nyqB, sigma, tw, s);
+  mark(5);
+  if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress: kernel launch failed: %s", cudaGetErrorString(err));
+  return DDS_OK;
+}
+
+}  // namespace dds

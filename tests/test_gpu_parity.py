@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances: the FP64 coefficient table matches the oracle's to 1e-12 of each
+component's largest magnitude; FP32 stresses match the FP64 direct sum of Eq. 10
+to a relative L2 error of 1e-5 per component (denominator max(||sigma_c||,
+1e-6 max_c' ||sigma_c'||)).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_TABLE = 1e-12
+TOL_STRESS = 1e-5
+
+
+@pytest.fixture(scope="module")
+def dds():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1804_01830_gb300 as mod
+    mod.load_library()
+    return mod
+
+
+def rel_l2_per_component(got, ref):
+    got = np.asarray(got, np.float64).reshape(6, -1)
+    ref = np.asarray(ref, np.float64).reshape(6, -1)
+    scale = max(np.linalg.norm(ref[c]) for c in range(6))
+    out = []
+    for c in range(6):
+        den = max(np.linalg.norm(ref[c]), 1e-6 * scale)
+        out.append(np.linalg.norm(got[c] - ref[c]) / den)
+    return np.array(out)
+
+
+def gpu_stress(dds, p, dtype=torch.float32, n_near=None):
+    ctx = dds.context_for(p, n_near=n_near)
+    rho = torch.from_numpy(p.rho.astype(np.float32)).to("cuda", dtype=dtype).contiguous()
+    sigma = ctx.stress(rho)
+    torch.cuda.synchronize()
+    out = sigma.cpu().numpy()
+    ctx.close()
+    return out
+
+
+def all_offsets(g):
+    k, j, i = np.meshgrid(np.arange(-(g.nz - 1), g.nz), np.arange(-(g.ny - 1), g.ny),
+                          np.arange(-(g.nx - 1), g.nx), indexing="ij")
+    return np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
+
+
+# ------------------------------------------------------------ table (P11) --
+@pytest.mark.parametrize("cells", [(1e-6, 1e-6, 0.25e-6), (0.5e-6, 0.5e-6, 0.2e-6), (0.2e-6, 0.2e-6, 0.02e-6)])
+def test_fp64_table_matches_oracle(dds, cells):
+    g = W.Geometry(12, 10, 7, *cells)
+    ctx = dds.StressContext(0)
+    ctx.set_geometry(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.mu, g.nu)
+    ijk = all_offsets(g)
+    t_all, b_all = W.gan_families()
+    for t, b in [(t_all[0], b_all[0]), (t_all[9], b_all[9]),
+                 ([0.0, 0.5, math.sqrt(3) / 2], [W.A_LATT / 2, math.sqrt(3) * W.A_LATT / 2, W.C_LATT])]:
+        got = ctx.table_at(t, b, ijk).reshape(2 * g.nz - 1, 2 * g.ny - 1, 2 * g.nx - 1, 6)
+        ref = oracle.gtable(g, t, b)
+        for c in range(6):
+            m = np.abs(ref[..., c]).max()
+            assert np.abs(got[..., c] - ref[..., c]).max() <= TOL_TABLE * m, c
+    ctx.close()
+
+
+def test_fp64_table_sampled_at_full_size(dds):
+    g = W.Geometry(256, 256, 128, 0.2e-6, 0.2e-6, 0.05e-6)
+    ctx = dds.StressContext(0)
+    ctx.set_geometry(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.mu, g.nu)
+    rng = np.random.default_rng(0)
+    ijk = np.concatenate([rng.integers(-255, 256, size=(200, 3)) * np.array([1, 1, 0]) +
+                          rng.integers(-127, 128, size=(200, 1)) * np.array([0, 0, 1]),
+                          rng.integers(-4, 5, size=(100, 3)),
+                          np.array([[255, 255, 127], [-255, -255, -127], [0, 0, 0], [0, 0, 1]])])
+    t_all, b_all = W.gan_families()
+    for f in (2, 11):
+        got = ctx.table_at(t_all[f], b_all[f], ijk)
+        ref = np.array([oracle.interaction(g, *o, t_all[f], b_all[f]) for o in ijk])
+        for c in range(6):
+            assert np.abs(got[:, c] - ref[:, c]).max() <= TOL_TABLE * np.abs(ref[:, c]).max()
+    ctx.close()
+
+
+# ------------------------------------------------------ stress vs oracle ---
+def test_gaussian_disk_32_full(dds):
+    p = W.gaussian_disk_32()
+    got = gpu_stress(dds, p)
+    ref = oracle.stress_direct(p.geom, p.t, p.b, p.rho).T
+    assert rel_l2_per_component(got, ref).max() <= TOL_STRESS
+
+
+@pytest.mark.parametrize("shape,cells,fams,seed", [
+    ((40, 24, 10), (0.2e-6, 0.2e-6, 0.05e-6), list(range(18)), 1),     # ragged sizes, all 18 families
+    ((33, 17, 9), (1e-6, 1e-6, 0.25e-6), [0, 7, 8], 2),                  # odd nx, one field per family
+    ((16, 64, 3), (0.5e-6, 0.5e-6, 0.2e-6), [1, 4, 6, 13, 17], 3),
+    ((64, 16, 16), (0.3e-6, 0.3e-6, 0.3e-6), [5, 10], 4),                # cubic cells (no subdivision)
+    ((7, 1, 1), (1e-6, 1e-6, 1e-6), [3, 12], 6),                         # a single line
+])
+def test_random_densities_vs_direct_sum(dds, shape, cells, fams, seed):
+    g = W.Geometry(*shape, *cells)
+    t, b = W.gan_families()
+    p = W.random_problem(g, t[fams], b[fams], seed=seed)
+    got = gpu_stress(dds, p)
+    ref = oracle.stress_direct(g, p.t, p.b, p.rho).T
+    assert rel_l2_per_component(got, ref).max() <= TOL_STRESS
+
+
+def test_single_cell_has_only_the_vanishing_self_term(dds):
+    # Sec. 2.3: the self-interaction coefficient vanishes; one cell alone gives sigma = 0
+    g = W.Geometry(1, 1, 1, 1e-6, 1e-6, 0.25e-6)
+    t, b = W.gan_families()
+    p = W.random_problem(g, t[[0, 9]], b[[0, 9]], seed=5)
+    got = gpu_stress(dds, p)
+    scale = g.mu * W.A_LATT * p.rho.max() * g.dz          # natural stress scale of one cell
+    assert np.abs(got).max() <= 1e-9 * scale
+
+
+def test_near_radius_option(dds):
+    g = W.Geometry(20, 18, 12, 0.2e-6, 0.2e-6, 0.05e-6)
+    t, b = W.gan_families()
+    p = W.random_problem(g, t[[0, 8]], b[[0, 8]], seed=9)
+    for n_near in (0.0, 5.0):
+        got = gpu_stress(dds, p, n_near=n_near)
+        ref = oracle.stress_direct(g, p.t, p.b, p.rho, n_near=n_near).T
+        assert rel_l2_per_component(got, ref).max() <= TOL_STRESS
+
+
+def sample_targets(g, n, seed):
+    rng = np.random.default_rng(seed)
+    pts = rng.integers(0, g.n_cells, size=n)
+    corners = [0, g.n_cells - 1, g.nx - 1, (g.ny - 1) * g.nx, (g.nz - 1) * g.nx * g.ny]
+    return np.unique(np.concatenate([pts, corners]))
+
+
+def test_radial_disk_512_sampled(dds):
+    p = W.radial_disk_512()
+    got = gpu_stress(dds, p).reshape(6, -1)
+    tg = sample_targets(p.geom, 24, seed=1)
+    ref = oracle.stress_direct(p.geom, p.t, p.b, p.rho, targets=tg, use_table=False).T
+    assert rel_l2_per_component(got[:, tg], ref).max() <= TOL_STRESS
+
+
+def test_gan_layer_256_sampled(dds):
+    p = W.gan_layer_256(0)
+    got = gpu_stress(dds, p).reshape(6, -1)
+    tg = sample_targets(p.geom, 12, seed=2)
+    ref = oracle.stress_direct(p.geom, p.t, p.b, p.rho, targets=tg, use_table=False).T
+    assert rel_l2_per_component(got[:, tg], ref).max() <= TOL_STRESS
+
+
+# ------------------------------------------------------------- properties ---
+def test_linearity_at_full_size(dds):
+    p = W.gan_layer_256(0)
+    ctx = dds.context_for(p)
+    r1 = torch.from_numpy(p.rho.astype(np.float32)).cuda()
+    r2 = torch.flip(r1, dims=[2]).contiguous()
+    s1 = ctx.stress(r1).double()
+    s2 = ctx.stress(r2).double()
+    s12 = ctx.stress((2.0 * r1 - 0.5 * r2).contiguous()).double()
+    torch.cuda.synchronize()
+    lhs = (s12 - (2.0 * s1 - 0.5 * s2)).cpu().numpy().reshape(6, -1)
+    ref = (2.0 * s1 - 0.5 * s2).cpu().numpy().reshape(6, -1)
+    assert rel_l2_per_component(lhs + ref, ref).max() <= 1e-5
+    ctx.close()
+
+
+def test_bf16_density_storage(dds):
+    p = W.random_problem(W.Geometry(24, 20, 8, 0.2e-6, 0.2e-6, 0.05e-6), *[a[[0, 9]] for a in W.gan_families()],
+                         seed=11)
+    got = gpu_stress(dds, p, dtype=torch.bfloat16)
+    rho_bf16 = torch.from_numpy(p.rho.astype(np.float32)).to(torch.bfloat16).float().double().numpy()
+    exact = oracle.stress_direct(p.geom, p.t, p.b, rho_bf16).T
+    assert rel_l2_per_component(got, exact).max() <= TOL_STRESS     # exact on bf16-rounded densities
+    full = oracle.stress_direct(p.geom, p.t, p.b, p.rho).T
+    assert rel_l2_per_component(got, full).max() <= 4e-3            # bf16 rounding of rho: 2^-8 relative
+
+
+# ---------------------------------------------------------- API surfaces ---
+def test_host_entry_point_matches_device_entry_point(dds):
+    p = W.gaussian_disk_32()
+    ctx = dds.context_for(p)
+    dev = ctx.stress(torch.from_numpy(p.rho.astype(np.float32)).cuda()).cpu().numpy()
+    host = ctx.stress_host(p.rho.astype(np.float32))
+    assert np.array_equal(dev, host)
+    ctx.close()
+
+
+def test_batched_matches_single_calls(dds):
+    probs = [W.gaussian_disk_32(), W.random_problem(W.Geometry(20, 12, 6, 0.5e-6, 0.5e-6, 0.2e-6),
+                                                    *[a[[2, 3, 14]] for a in W.gan_families()], seed=3)]
+    ctxs = [dds.context_for(p) for p in probs]
+    rhos = [torch.from_numpy(p.rho.astype(np.float32)).cuda() for p in probs]
+    singles = [c.stress(r).cpu().numpy() for c, r in zip(ctxs, rhos)]
+    outs = [torch.empty((6,) + c.shape, device="cuda") for c in ctxs]
+    dds.dds_stress_batched([c.handle for c in ctxs], [r.data_ptr() for r in rhos], [dds.DDS_F32] * 2,
+                           [o.data_ptr() for o in outs])
+    torch.cuda.synchronize()
+    for s, o in zip(singles, outs):
+        assert np.array_equal(s, o.cpu().numpy())
+    for c in ctxs:
+        c.close()
+
+
+def test_error_codes(dds):
+    ctx = dds.StressContext(0)
+    with pytest.raises(dds.DDSError) as ei:
+        ctx.build_kernels()
+    assert ei.value.code == dds.DDS_ERR_NOT_READY
+    with pytest.raises(dds.DDSError) as ei:
+        ctx.set_geometry(0, 4, 4, 1e-6, 1e-6, 1e-6, 1e9, 0.3)
+    assert ei.value.code == dds.DDS_ERR_INVALID_ARG
+    with pytest.raises(dds.DDSError) as ei:
+        ctx.set_geometry(1024, 4, 4, 1e-6, 1e-6, 1e-6, 1e9, 0.3)
+    assert ei.value.code == dds.DDS_ERR_UNSUPPORTED
+    ctx.set_geometry(8, 8, 4, 1e-6, 1e-6, 1e-6, 1e9, 0.3)
+    with pytest.raises(dds.DDSError) as ei:
+        ctx.set_families([[0, 0, 0]], [[1e-10, 0, 0]])
+    assert ei.value.code == dds.DDS_ERR_INVALID_ARG
+    ctx.set_families([[0, 0, 1]], [[1e-10, 0, 0]])
+    rho = torch.zeros((1, 4, 8, 8), device="cuda")
+    with pytest.raises(dds.DDSError) as ei:
+        ctx.stress(rho)
+    assert ei.value.code == dds.DDS_ERR_NOT_READY
+    ctx.build_kernels()
+    assert float(ctx.stress(rho).abs().max()) == 0.0
+    assert ctx.launches_per_stress == 5
+    ctx.close()

@@ -51,6 +51,12 @@ def parse():
     return ap.parse_args()
 
 
+def _json_default(o):
+    if isinstance(o, (np.floating, np.integer)):
+        return o.item()
+    raise TypeError(f"not JSON serialisable: {type(o)}")
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -200,7 +206,7 @@ def run_reference(args):
                                    f"{p.geom.n_cells} source cells x {p.n_families} families"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, default=_json_default), flush=True)
     return 0
 
 
@@ -225,7 +231,7 @@ def run_ours(args):
     g = p.geom
     ctx = dds.context_for(p, device=local)
     q = ctx.query()
-    rho = torch.from_numpy(p.rho.astype(np.float32)).cuda()
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho, dtype=np.float32)).cuda()
     sigma = torch.empty((6,) + g.shape, dtype=torch.float32, device="cuda")
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -276,7 +282,7 @@ def run_ours(args):
     # end to end through the host-buffer entry point, pinned buffers
     e2e = None
     if not args.no_e2e:
-        rho_h = torch.from_numpy(p.rho.astype(np.float32)).pin_memory()
+        rho_h = torch.from_numpy(np.ascontiguousarray(p.rho, dtype=np.float32)).pin_memory()
         sig_h = torch.empty((6,) + g.shape, dtype=torch.float32).pin_memory()
         rh, sh = rho_h.numpy(), sig_h.numpy()
         for _ in range(2):
@@ -324,7 +330,7 @@ def run_ours(args):
         "clocks": clk,
     }
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, default=_json_default), flush=True)
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()

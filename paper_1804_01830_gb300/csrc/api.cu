@@ -209,10 +209,11 @@ int make_plan(dds_ctx *ctx) {
   sh.wz = 0;
   const size_t pref = 110 * 1024, cap = 220 * 1024;
   for (int pass = 0; pass < 2 && sh.wz == 0; ++pass) {
-    for (int W : {64, 32, 16, 8}) {
+    for (int W : {64, 32, 16, 8, 4}) {
       if (W > sh.M || sh.py % W != 0) continue;
-      if (W * sh.pz > 2048 && W != 8) continue;
-      const size_t smem = sizeof(float2) * (size_t)(std::max(sh.fe, 1) + 1) * sh.pz * W;
+      if (W * sh.pz > 2048 && W > 8) continue;
+      const size_t fe = (size_t)std::max(sh.fe, 1);
+      const size_t smem = (sizeof(float2) * (fe + 1) + sizeof(float) * fe) * sh.pz * W;
       if (smem <= (pass == 0 ? pref : cap)) { sh.wz = W; break; }
     }
   }

@@ -119,6 +119,18 @@ template <> struct Plan<256>  { static constexpr int n = 2, r0 = 16, r1 = 16, r2
 template <> struct Plan<512>  { static constexpr int n = 3, r0 = 8,  r1 = 8, r2 = 8; };
 template <> struct Plan<1024> { static constexpr int n = 3, r0 = 16, r1 = 8, r2 = 8; };
 
+// Asynchronous global -> shared copies (cp.async): every thread issues all of
+// its copies before waiting, so a whole tile is in flight at once.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Twiddle tables: for every power of two P in [16, 2048] the values
 // exp(-2 pi i k / P), k = 0..P-1, stored back to back starting at offset P - 16.
 __host__ __device__ constexpr int tw_offset(int P) { return P - 16; }

@@ -54,7 +54,20 @@ __global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, const void
   const float2 *twM = tw + tw_offset(M);
   const float2 *tw2 = tw + tw_offset(2 * M);
 
+  // A group with one family (coefficient c) needs no combination: its line pairs are
+  // copied straight into the transposed tile and the spectrum is scaled by c.
+  const bool direct = !BF16 && even && col.nf[g] == 1 && col.nd[g] == 1;
   for (int d = 0; d < col.nd[g]; ++d) {
+    float scale_out = 1.0f;
+    if (direct) {
+      scale_out = col.coef[col.f0[g]][0];
+      const float *r = (const float *)rho_v + (long)col.fam[col.f0[g]] * N + l0 * sh.nx;
+      for (int p = tid; p < W * nxh; p += NT) {
+        const int w = p / nxh, n = p - w * nxh;
+        if (l0 + w < L) cp_async8(&buf[n * LD + w], r + (long)w * sh.nx + 2 * n);
+        else buf[n * LD + w] = make_float2(0.f, 0.f);
+      }
+    } else {
     float2 acc[OWN];
 #pragma unroll
     for (int i = 0; i < OWN; ++i) acc[i] = make_float2(0.f, 0.f);
@@ -97,10 +110,12 @@ __global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, const void
         buf[n * LD + w] = acc[i];
       }
     }
+    }
     for (int p = W * nxh + tid; p < W * (M / 2); p += NT) {   // zero the tail of the non-zero half
       const int w = p % W, n = p / W;
       buf[n * LD + w] = make_float2(0.f, 0.f);
     }
+    cp_async_wait_all();
     __syncthreads();
     fft_tile<M, W, LD, NT, false, true, false>(buf, twM, tid);
     const int e = col.e0[g] + d;
@@ -114,12 +129,13 @@ __global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, const void
       const float2 O = make_float2(0.5f * (a.y + c.y), -0.5f * (a.x - c.x));
       const float2 wk = __ldg(tw2 + k);
       float2 X;
-      X.x = E.x + (wk.x * O.x - wk.y * O.y);
-      X.y = E.y + (wk.x * O.y + wk.y * O.x);
+      X.x = scale_out * (E.x + (wk.x * O.x - wk.y * O.y));
+      X.y = scale_out * (E.y + (wk.x * O.y + wk.y * O.x));
       out_main[((long)e * L + line) * M + k] = X;
       if (k == 0) {
         const int z = (int)(line / sh.ny), y = (int)(line - (long)z * sh.ny);
-        out_nyq[((long)e * sh.ny + y) * sh.nz + z] = make_float2(E.x - O.x, E.y - O.y);   // W^M = -1
+        out_nyq[((long)e * sh.ny + y) * sh.nz + z] =
+            make_float2(scale_out * (E.x - O.x), scale_out * (E.y - O.y));   // W^M = -1
       }
     }
     __syncthreads();
@@ -162,13 +178,23 @@ __global__ void __launch_bounds__(NT) k_ypass(Shape sh, int nf, const float2 *in
     rs = nz;
     ncols = min(W, nz - zt * W);
   }
-  for (int p = tid; p < rows_in * W; p += NT) {
-    const int n = p / W, w = p - n * W;
-    buf[n * LD + w] = (w < ncols) ? in[n * rs + w] : make_float2(0.f, 0.f);
+  if (tau < tiles_main) {            // rows of W complex, 16-byte aligned: 16-byte copies
+    constexpr int H = W / 2;
+    for (int p = tid; p < rows_in * H; p += NT) {
+      const int n = p / H, c2 = p - n * H;
+      cp_async16(&buf[n * LD + 2 * c2], &in[n * rs + 2 * c2]);
+    }
+  } else {
+    for (int p = tid; p < rows_in * W; p += NT) {
+      const int n = p / W, w = p - n * W;
+      if (w < ncols) cp_async8(&buf[n * LD + w], &in[n * rs + w]);
+      else buf[n * LD + w] = make_float2(0.f, 0.f);
+    }
   }
   if (!INV) {
     for (int p = rows_in * W + tid; p < (PY / 2) * W; p += NT) buf[p] = make_float2(0.f, 0.f);
   }
+  cp_async_wait_all();
   __syncthreads();
   fft_tile<PY, W, LD, NT, INV, !INV, INV>(buf, tw + tw_offset(PY), tid);
   for (int p = tid; p < rows_out * W; p += NT) {
@@ -178,6 +204,9 @@ __global__ void __launch_bounds__(NT) k_ypass(Shape sh, int nf, const float2 *in
 }
 
 // ------------------------------------------------------------- fused z ------
+// Shared memory: fe field tiles [PZ][W], one output tile [PZ][W], and the kernel
+// spectra of one stress component for this tile [fe][PZ][W] (FP32).  The spectra
+// of component c+1 stream in (cp.async) while component c is inverted and stored.
 template <int PZ, int W>
 __global__ void __launch_bounds__(NT) k_zpass(Shape sh, const float2 *in_main, const float2 *in_nyq,
                                               const float *kspec, float2 *out_main, float2 *out_nyq,
@@ -188,6 +217,7 @@ __global__ void __launch_bounds__(NT) k_zpass(Shape sh, const float2 *in_main, c
   const int M = sh.M, py = sh.py, nz = sh.nz, fe = sh.fe;
   float2 *fields = smem;            // [fe][PZ][W]
   float2 *obuf = smem + (long)fe * TS;
+  float *gbuf = reinterpret_cast<float *>(obuf + TS);   // [fe][PZ][W]
   const long ktiles = M / W;
   const long tiles_main = (long)py * ktiles;
   const long tau = blockIdx.x;
@@ -199,36 +229,53 @@ __global__ void __launch_bounds__(NT) k_zpass(Shape sh, const float2 *in_main, c
   } else {
     ky0 = (tau - tiles_main) * W;
   }
-  // load rows z < nz of every field; zero rows [nz, PZ/2)
+  const float *ks = kspec + tau * 6L * fe * TS;
+  const int gchunks = fe * TS / 4;   // 16-byte chunks of one component's spectra
+  // rows z < nz of every field, and the spectra of component 0
   for (int e = 0; e < fe; ++e) {
     float2 *f = fields + (long)e * TS;
     if (!nyq) {
+      constexpr int H = W / 2;
       const float2 *src = in_main + ((long)e * nz * py + ky) * M + kx0;
-      for (int p = tid; p < nz * W; p += NT) {
-        const int z = p / W, w = p - z * W;
-        f[z * LD + w] = src[(long)z * py * M + w];
+      for (int p = tid; p < nz * H; p += NT) {
+        const int z = p / H, c2 = p - z * H;
+        cp_async16(&f[z * LD + 2 * c2], &src[(long)z * py * M + 2 * c2]);
       }
     } else {
       const float2 *src = in_nyq + ((long)e * py + ky0) * nz;
       for (int p = tid; p < nz * W; p += NT) {
         const int w = p / nz, z = p - w * nz;
-        f[z * LD + w] = src[(long)w * nz + z];
+        cp_async8(&f[z * LD + w], &src[(long)w * nz + z]);
       }
     }
     for (int p = nz * W + tid; p < (PZ / 2) * W; p += NT) f[p] = make_float2(0.f, 0.f);
   }
+  for (int q = tid; q < gchunks; q += NT) cp_async16(gbuf + 4 * q, ks + 4 * q);
+  cp_async_wait_all();
   __syncthreads();
   const float2 *twP = tw + tw_offset(PZ);
   for (int e = 0; e < fe; ++e) fft_tile<PZ, W, LD, NT, false, true, false>(fields + (long)e * TS, twP, tid);
 
-  const float *ks = kspec + tau * 6L * fe * TS;
   for (int c = 0; c < 6; ++c) {
-    for (int p = tid; p < TS; p += NT) {
-      float2 acc = make_float2(0.f, 0.f);
-      for (int e = 0; e < fe; ++e) acc = cmadd_i(acc, __ldg(ks + ((long)c * fe + e) * TS + p), fields[(long)e * TS + p]);
-      obuf[p] = acc;
+    for (int q = tid; q < TS / 4; q += NT) {          // four consecutive positions per thread
+      float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+      for (int e = 0; e < fe; ++e) {
+        const float4 g = *reinterpret_cast<const float4 *>(gbuf + (long)e * TS + 4 * q);
+        const float4 r01 = *reinterpret_cast<const float4 *>(fields + (long)e * TS + 4 * q);
+        const float4 r23 = *reinterpret_cast<const float4 *>(fields + (long)e * TS + 4 * q + 2);
+        a0 = cmadd_i(a0, g.x, make_float2(r01.x, r01.y));
+        a1 = cmadd_i(a1, g.y, make_float2(r01.z, r01.w));
+        a2 = cmadd_i(a2, g.z, make_float2(r23.x, r23.y));
+        a3 = cmadd_i(a3, g.w, make_float2(r23.z, r23.w));
+      }
+      *reinterpret_cast<float4 *>(obuf + 4 * q) = make_float4(a0.x, a0.y, a1.x, a1.y);
+      *reinterpret_cast<float4 *>(obuf + 4 * q + 2) = make_float4(a2.x, a2.y, a3.x, a3.y);
     }
     __syncthreads();
+    if (c < 5) {
+      const float *kn = ks + (long)(c + 1) * fe * TS;
+      for (int q = tid; q < gchunks; q += NT) cp_async16(gbuf + 4 * q, kn + 4 * q);
+    }
     fft_tile<PZ, W, LD, NT, true, false, true>(obuf, twP, tid);
     if (!nyq) {
       float2 *dst = out_main + ((long)c * nz * py + ky) * M + kx0;
@@ -243,6 +290,7 @@ __global__ void __launch_bounds__(NT) k_zpass(Shape sh, const float2 *in_main, c
         dst[(long)w * nz + z] = obuf[z * LD + w];
       }
     }
+    cp_async_wait_all();
     __syncthreads();
   }
 }
@@ -260,7 +308,8 @@ __global__ void __launch_bounds__(NT) k_x_inv(Shape sh, const float2 *in_main, c
   const long l0 = (long)blockIdx.x * W;
   for (int p = tid; p < W * M; p += NT) {
     const int w = p / M, k = p - w * M;
-    buf[k * LD + w] = (l0 + w < L) ? in_main[(l0 + w) * M + k] : make_float2(0.f, 0.f);
+    if (l0 + w < L) cp_async8(&buf[k * LD + w], &in_main[(l0 + w) * M + k]);
+    else buf[k * LD + w] = make_float2(0.f, 0.f);
   }
   if (tid < W) {
     const long line = l0 + tid;
@@ -273,6 +322,7 @@ __global__ void __launch_bounds__(NT) k_x_inv(Shape sh, const float2 *in_main, c
     }
     xm[tid] = v;
   }
+  cp_async_wait_all();
   __syncthreads();
   // Z[k] = (X[k] + conj X[M-k]) + i W^-k (X[k] - conj X[M-k]); pairs (k, M-k) per thread
   const float2 *tw2 = tw + tw_offset(2 * M);
@@ -321,7 +371,6 @@ cudaError_t prep(K kernel, size_t smem) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-int y_width(int py) { return py >= 1024 ? 8 : 16; }
 
 template <int M>
 cudaError_t launch_x_fwd(const Shape &sh, const Collapse &col, const void *rho, bool bf16, float2 *om,
@@ -355,7 +404,7 @@ cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in
 template <int PZ, int W>
 cudaError_t launch_z(const Shape &sh, const float2 *im, const float2 *in, const float *ks, float2 *om,
                      float2 *on, const float2 *tw, cudaStream_t s) {
-  const size_t smem = sizeof(float2) * (size_t)(sh.fe + 1) * PZ * W;
+  const size_t smem = (sizeof(float2) * (size_t)(sh.fe + 1) + sizeof(float) * (size_t)sh.fe) * PZ * W;
   const long tiles = (long)sh.py * (sh.M / W) + sh.py / W;
   cudaError_t err = prep(k_zpass<PZ, W>, smem);
   if (err != cudaSuccess) return err;
@@ -401,11 +450,11 @@ cudaError_t dispatch_y(const Shape &sh, int nf, const float2 *im, const float2 *
   }
 }
 
-// Tile widths the planner can choose: W * PZ <= 2048, or W = 8.
+// Tile widths the planner can choose: W * PZ <= 2048, or W <= 8.
 template <int PZ, int W>
 cudaError_t launch_z_if(const Shape &sh, const float2 *im, const float2 *in, const float *ks, float2 *om,
                         float2 *on, const float2 *tw, cudaStream_t s) {
-  if constexpr (W * PZ <= 2048 || W == 8) return launch_z<PZ, W>(sh, im, in, ks, om, on, tw, s);
+  if constexpr (W * PZ <= 2048 || W <= 8) return launch_z<PZ, W>(sh, im, in, ks, om, on, tw, s);
   return cudaErrorInvalidValue;
 }
 
@@ -413,6 +462,7 @@ template <int PZ>
 cudaError_t dispatch_z_w(const Shape &sh, const float2 *im, const float2 *in, const float *ks, float2 *om,
                          float2 *on, const float2 *tw, cudaStream_t s) {
   switch (sh.wz) {
+    case 4: return launch_z_if<PZ, 4>(sh, im, in, ks, om, on, tw, s);
     case 8: return launch_z_if<PZ, 8>(sh, im, in, ks, om, on, tw, s);
     case 16: return launch_z_if<PZ, 16>(sh, im, in, ks, om, on, tw, s);
     case 32: return launch_z_if<PZ, 32>(sh, im, in, ks, om, on, tw, s);

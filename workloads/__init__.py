@@ -88,6 +88,11 @@ class Problem:
     rho: np.ndarray          # (F, nz, ny, nx) float64, m^-2
     meta: dict = field(default_factory=dict)
 
+    def __post_init__(self):
+        self.t = np.ascontiguousarray(self.t, dtype=np.float64).reshape(-1, 3)
+        self.b = np.ascontiguousarray(self.b, dtype=np.float64).reshape(-1, 3)
+        self.rho = np.ascontiguousarray(self.rho, dtype=np.float64)
+
     @property
     def n_families(self) -> int:
         return int(self.t.shape[0])

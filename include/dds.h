@@ -57,9 +57,14 @@ enum { DDS_F32 = 0, DDS_BF16 = 1 };
 
 /* Option keys for dds_set_option. */
 enum {
-  DDS_OPT_NEAR_RADIUS = 1  /* near-field radius in units of the largest cell edge
+  DDS_OPT_NEAR_RADIUS = 1, /* near-field radius in units of the largest cell edge
                               (Sec. 2.3 "several nearest-neighbour shells"); default 3;
                               0 disables subdivision.  Invalidates built kernels. */
+  DDS_OPT_Z_LANES = 2      /* schedule of the fused z pass: 0 = automatic (default);
+                              -1 = shared-memory tiles; 1, 2, 4, 8 = register-only kernel
+                              with that many lanes per (kx, ky) column (needs padded
+                              z size <= 64 and <= 4 combined fields).  Same result up to
+                              rounding; a tuning knob.  Invalidates built kernels. */
 };
 
 /* Limits of this build. */

@@ -207,6 +207,20 @@ int make_plan(dds_ctx *ctx) {
   sh.fin = ctx->F;
   sh.fe = ctx->fe;
   sh.wz = 0;
+  sh.zreg_g = 0;
+  if (sh.pz <= 64 && sh.fe <= 4 && ctx->z_lanes >= 0) {
+    // register-only z pass: E = pz / G registers per lane, E in {8, 16}
+    int G = ctx->z_lanes;
+    if (G == 0) G = sh.pz / 16 < 1 ? 1 : (sh.fe >= 2 ? sh.pz / 8 : sh.pz / 16);   // default
+    const int E = sh.pz / G;
+    if ((E == 8 || E == 16) && sh.pz % G == 0 && sh.M >= 32 / G) {
+      sh.zreg_g = G;
+      ctx->shape = sh;
+      return DDS_OK;
+    }
+    if (ctx->z_lanes > 0)
+      return fail(ctx, DDS_ERR_UNSUPPORTED, "z pass: %d lanes per column not available for pz %d", G, sh.pz);
+  }
   const size_t pref = 110 * 1024, cap = 220 * 1024;
   for (int pass = 0; pass < 2 && sh.wz == 0; ++pass) {
     for (int W : {64, 32, 16, 8, 4}) {
@@ -231,8 +245,7 @@ int alloc_buffers(dds_ctx *ctx) {
   const size_t b = std::max(fe * nz * py * M, 6 * nz * ny * M);
   const size_t na = std::max(fe * ny * nz, 6 * py * nz);
   const size_t nb = std::max(fe * py * nz, 6 * ny * nz);
-  const size_t tiles = py * (M / sh.wz) + py / sh.wz;
-  const size_t ks = tiles * 6 * fe * pz * sh.wz;
+  const size_t ks = py * (M + 1) * pz * 6 * fe;   // one FP32 value per (k, component, field)
   free_buffers(ctx);
   cudaError_t err = cudaMalloc(&ctx->bufA, a * sizeof(float2));
   if (err == cudaSuccess) err = cudaMalloc(&ctx->bufB, b * sizeof(float2));
@@ -342,6 +355,12 @@ int dds_set_families(dds_ctx *ctx, int F, const double *t, const double *b) {
 int dds_set_option(dds_ctx *ctx, int key, double value) {
   if (!ctx) return DDS_ERR_INVALID_ARG;
   switch (key) {
+    case DDS_OPT_Z_LANES:
+      if (!(value == -1 || value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
+        return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: z lanes must be -1, 0, 1, 2, 4 or 8");
+      ctx->z_lanes = (int)value;
+      invalidate(ctx);
+      return DDS_OK;
     case DDS_OPT_NEAR_RADIUS:
       if (!(value >= 0.0) || !isfinite(value))
         return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: near radius must be >= 0");

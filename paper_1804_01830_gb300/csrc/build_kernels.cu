@@ -262,27 +262,44 @@ __global__ void __launch_bounds__(256) k_cols_d(double2 *data, long os, long rs,
   }
 }
 
-// Imaginary part of the spectrum of component c of field e, scaled, into the
-// z-pass tile layout kspec[tile][6][fe][pz][wz].
-__global__ void k_extract(const double2 *spec, int M, int py, int pz, int wz, int fe, int e, int c,
+// Imaginary part of the spectrum of component c of field e, scaled, into the layout
+// the fused z pass reads:
+//   shared-memory variant (zg = 0): kspec[tile][6][fe][pz][wz], tiles of wz columns;
+//   register variant (zg = G > 0):  kspec[warp tile][6][fe][lane][E], E = pz / G, warp
+//     tiles of 32/G columns, lane g * (32/G) + w holding kz = k1 + E bitrev_G(g), k1 < E.
+// Main tiles cover (ky, kx < M) row by row; the Nyquist tiles (kx = M) follow.
+__global__ void k_extract(const double2 *spec, int M, int py, int pz, int wz, int zg, int fe, int e, int c,
                           double scale, float *kspec) {
-  const long tiles_main = (long)py * (M / wz);
-  const long tiles = tiles_main + py / wz;
-  const long per_tile = (long)pz * wz;
+  const int cw = zg > 0 ? 32 / zg : wz;                  // columns per tile
+  const int E = zg > 0 ? pz / zg : 0;                     // registers per lane
+  const long per_tile = zg > 0 ? 32L * E : (long)pz * wz;
+  const long tiles_main = (long)py * (M / cw);
+  const long tiles = tiles_main + py / cw;
   const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (idx >= tiles * per_tile) return;
   const long tau = idx / per_tile;
-  const int kz = (int)((idx % per_tile) / wz), w = (int)(idx % wz);
+  const int r = (int)(idx % per_tile);
+  int kz, w;
+  if (zg > 0) {
+    const int lane = r / E, k1 = r % E, g = lane / cw;
+    const int gb = zg == 4 ? (((g & 1) << 1) | (g >> 1))
+                 : zg == 8 ? (((g & 1) << 2) | (g & 2) | (g >> 2)) : g;
+    w = lane % cw;
+    kz = k1 + E * gb;
+  } else {
+    kz = r / wz;
+    w = r % wz;
+  }
   int kx, ky;
   if (tau < tiles_main) {
-    ky = (int)(tau / (M / wz));
-    kx = (int)(tau % (M / wz)) * wz + w;
+    ky = (int)(tau / (M / cw));
+    kx = (int)(tau % (M / cw)) * cw + w;
   } else {
-    ky = (int)(tau - tiles_main) * wz + w;
+    ky = (int)(tau - tiles_main) * cw + w;
     kx = M;
   }
   const double v = spec[((long)kz * py + ky) * (M + 1) + kx].y;
-  kspec[(((tau * 6 + c) * fe + e) * pz + kz) * wz + w] = (float)(v * scale);
+  kspec[((tau * 6 + c) * fe + e) * per_tile + r] = (float)(v * scale);
 }
 
 template <int M>
@@ -422,9 +439,9 @@ int build_spectra(dds_ctx *ctx, cudaStream_t s) {
       if (err == cudaSuccess)   // z: one batch, rows kz, columns (ky, kx)
         err = cols_dispatch(pz, spec, 1, 0, (long)py * (M + 1), (long)py * (M + 1), ctx->tw.f64, s);
       if (err == cudaSuccess) {
-        const long n = ((long)py * (M / sh.wz) + py / sh.wz) * pz * sh.wz;
-        k_extract<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(spec, M, py, pz, sh.wz, sh.fe, e, c, scale,
-                                                              ctx->kspec);
+        const long n = (long)py * (M + 1) * pz;
+        k_extract<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(spec, M, py, pz, sh.wz, sh.zreg_g, sh.fe, e, c,
+                                                              scale, ctx->kspec);
         err = cudaGetLastError();
       }
     }

@@ -28,7 +28,8 @@ struct Shape {
   int M;              // px / 2 (complex length of the x transform)
   int py, pz;         // padded y and z sizes
   int fin, fe;        // input families, effective fields
-  int wz;             // columns per tile of the fused z pass
+  int wz;             // columns per tile of the fused z pass (shared-memory variant)
+  int zreg_g;         // > 0: register-only z pass, pz = 16 * zreg_g, zreg_g lanes per column
 };
 
 // FP64 description of a box coefficient (Eq. 9b times the cell volume).
@@ -55,6 +56,7 @@ struct dds_ctx {
   double h[3] = {0, 0, 0};
   double mu = 0, nu = 0;
   double n_near = 3.0;
+  int z_lanes = 0;                      // fused z pass: 0 auto, -1 shared-memory kernel, G lanes/column
   // families
   bool has_fam = false;
   int F = 0;

@@ -295,6 +295,168 @@ __global__ void __launch_bounds__(NT) k_zpass(Shape sh, const float2 *in_main, c
   }
 }
 
+// ------------------------------------------------- fused z, registers only ---
+// For pz = E G (E = 8 or 16 registers, G = 1..8 lanes per column): a warp owns
+// CW = 32 / G adjacent columns; lane g of a column holds elements n = g + G m
+// (m < E) of each field.  Four-step FFT: E-point DFT over m in registers, twiddle
+// W_pz^(g k1), G-point DFT across the G lanes by shuffles.  Lane g then holds
+// k = k1 + E bitrev_G(g); the contraction with the kernel spectra (laid out per warp
+// tile, lane, k1) runs in registers, and the inverse retraces the steps.  No shared
+// memory and no barriers; the next component's spectra load while the current one
+// is inverted and stored.
+template <int G>
+__device__ __forceinline__ int bitrev_lane(int g) {
+  if (G == 4) return ((g & 1) << 1) | (g >> 1);
+  if (G == 8) return ((g & 1) << 2) | (g & 2) | (g >> 2);
+  return g;
+}
+
+// a * W_8^q (forward) or a * conj(W_8^q) (inverse), q in 0..3 chosen per lane
+template <bool INV>
+__device__ __forceinline__ float2 rot8(float2 a, int q) {
+  const float r = 0.70710678118654752440f;
+  if (q == 0) return a;
+  if (q == 2) return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+  if (q == 1) return INV ? make_float2(r * (a.x - a.y), r * (a.x + a.y)) : make_float2(r * (a.x + a.y), r * (a.y - a.x));
+  return INV ? make_float2(-r * (a.x + a.y), r * (a.x - a.y)) : make_float2(r * (a.y - a.x), -r * (a.x + a.y));
+}
+
+template <int E, int G, bool INV>
+__device__ __forceinline__ void cross_lane_dft(float2 (&v)[E], int g, int cw) {
+  if constexpr (G == 1) return;
+  if (!INV) {   // decimation in frequency: natural in, bit-reversed out
+#pragma unroll
+    for (int h = G / 2; h >= 1; h >>= 1) {
+      const bool upper = (g & h) != 0;
+      const int q = (g & (h - 1)) * (4 / h);
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        float2 p;
+        p.x = __shfl_xor_sync(0xffffffffu, v[k].x, h * cw);
+        p.y = __shfl_xor_sync(0xffffffffu, v[k].y, h * cw);
+        v[k] = upper ? rot8<false>(csub(p, v[k]), q) : cadd(v[k], p);
+      }
+    }
+  } else {      // decimation in time: bit-reversed in, natural out
+#pragma unroll
+    for (int h = 1; h < G; h <<= 1) {
+      const bool upper = (g & h) != 0;
+      const int q = (g & (h - 1)) * (4 / h);
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        float2 p;
+        p.x = __shfl_xor_sync(0xffffffffu, v[k].x, h * cw);
+        p.y = __shfl_xor_sync(0xffffffffu, v[k].y, h * cw);
+        v[k] = upper ? csub(p, rot8<true>(v[k], q)) : cadd(v[k], rot8<true>(p, q));
+      }
+    }
+  }
+}
+
+template <int E, int G, int FE>
+__global__ void __launch_bounds__(128) k_zreg(Shape sh, const float2 *in_main, const float2 *in_nyq,
+                                              const float *kspec, float2 *out_main, float2 *out_nyq,
+                                              const float2 *tw) {
+  constexpr int P = G * E, CW = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const long T = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int M = sh.M, py = sh.py, nz = sh.nz, fe = sh.fe;
+  const long wt_main = (long)py * (M / CW);
+  const long wt_all = wt_main + py / CW;
+  if (T >= wt_all) return;                              // whole warp exits together
+  const int g = lane / CW, wl = lane - g * CW;
+  const bool nyq = T >= wt_main;
+  long ky = 0, kx = 0;
+  if (!nyq) {
+    ky = T / (M / CW);
+    kx = (T - ky * (M / CW)) * CW + wl;
+  } else {
+    ky = (T - wt_main) * CW + wl;
+  }
+  const float2 *twP = tw + tw_offset(P);
+
+  float2 f[FE][E];
+#pragma unroll
+  for (int e = 0; e < FE; ++e) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) f[e][m] = make_float2(0.f, 0.f);
+    if (e < fe) {
+#pragma unroll
+      for (int m = 0; m < E / 2; ++m) {
+        const int z = g + G * m;
+        if (z < nz) {
+          f[e][m] = !nyq ? __ldg(in_main + (((long)e * nz + z) * py + ky) * M + kx)
+                         : __ldg(in_nyq + ((long)e * py + ky) * nz + z);
+        }
+      }
+    }
+  }
+  // kernel spectra of component 0, in flight while the fields are transformed
+  const float *ks = kspec + (T * 6L * fe) * 32 * E;
+  float4 gv[FE][E / 4];
+#pragma unroll
+  for (int e = 0; e < FE; ++e) {
+    if (e < fe) {
+      const float4 *gp = reinterpret_cast<const float4 *>(ks + ((long)e * 32 + lane) * E);
+#pragma unroll
+      for (int q = 0; q < E / 4; ++q) gv[e][q] = __ldg(gp + q);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < FE; ++e) {
+    if (e < fe) {
+      dft_reg<E, false>(f[e]);
+      if (G > 1) {
+#pragma unroll
+        for (int k = 1; k < E; ++k) f[e][k] = cmul_tw<false>(f[e][k], __ldg(twP + g * k));
+      }
+      cross_lane_dft<E, G, false>(f[e], g, CW);
+    }
+  }
+  for (int c = 0; c < 6; ++c) {
+    float2 s[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) s[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int e = 0; e < FE; ++e) {
+      if (e < fe) {
+#pragma unroll
+        for (int q = 0; q < E / 4; ++q) {
+          const float4 g4 = gv[e][q];
+          s[4 * q + 0] = cmadd_i(s[4 * q + 0], g4.x, f[e][4 * q + 0]);
+          s[4 * q + 1] = cmadd_i(s[4 * q + 1], g4.y, f[e][4 * q + 1]);
+          s[4 * q + 2] = cmadd_i(s[4 * q + 2], g4.z, f[e][4 * q + 2]);
+          s[4 * q + 3] = cmadd_i(s[4 * q + 3], g4.w, f[e][4 * q + 3]);
+        }
+      }
+    }
+    if (c < 5) {   // next component's spectra fly while this one is inverted and stored
+#pragma unroll
+      for (int e = 0; e < FE; ++e) {
+        if (e < fe) {
+          const float4 *gp = reinterpret_cast<const float4 *>(ks + (((long)(c + 1) * fe + e) * 32 + lane) * E);
+#pragma unroll
+          for (int q = 0; q < E / 4; ++q) gv[e][q] = __ldg(gp + q);
+        }
+      }
+    }
+    cross_lane_dft<E, G, true>(s, g, CW);
+    if (G > 1) {
+#pragma unroll
+      for (int k = 1; k < E; ++k) s[k] = cmul_tw<true>(s[k], __ldg(twP + g * k));
+    }
+    dft_reg<E, true>(s);
+#pragma unroll
+    for (int m = 0; m < E / 2; ++m) {
+      const int z = g + G * m;
+      if (z < nz) {
+        if (!nyq) out_main[(((long)c * nz + z) * py + ky) * M + kx] = s[m];
+        else out_nyq[((long)c * py + ky) * nz + z] = s[m];
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- x inverse --
 template <int M>
 __global__ void __launch_bounds__(NT) k_x_inv(Shape sh, const float2 *in_main, const float2 *in_nyq,
@@ -471,8 +633,36 @@ cudaError_t dispatch_z_w(const Shape &sh, const float2 *im, const float2 *in, co
   }
 }
 
+template <int E, int G, int FE>
+cudaError_t launch_zreg(const Shape &sh, const float2 *im, const float2 *in, const float *ks, float2 *om,
+                        float2 *on, const float2 *tw, cudaStream_t s) {
+  constexpr int CW = 32 / G;
+  const long warps = (long)sh.py * (sh.M / CW) + sh.py / CW;
+  k_zreg<E, G, FE><<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(sh, im, in, ks, om, on, tw);
+  return cudaGetLastError();
+}
+
+template <int E, int G>
+cudaError_t dispatch_zreg_fe(const Shape &sh, const float2 *im, const float2 *in, const float *ks, float2 *om,
+                             float2 *on, const float2 *tw, cudaStream_t s) {
+  if (sh.fe <= 1) return launch_zreg<E, G, 1>(sh, im, in, ks, om, on, tw, s);
+  if (sh.fe <= 2) return launch_zreg<E, G, 2>(sh, im, in, ks, om, on, tw, s);
+  return launch_zreg<E, G, 4>(sh, im, in, ks, om, on, tw, s);
+}
+
 cudaError_t dispatch_z(const Shape &sh, const float2 *im, const float2 *in, const float *ks, float2 *om,
                        float2 *on, const float2 *tw, cudaStream_t s) {
+  if (sh.zreg_g > 0) {
+    switch (sh.pz * 16 + sh.zreg_g) {   // (pz, lanes per column) -> E = pz / G registers
+      case 16 * 16 + 1: return dispatch_zreg_fe<16, 1>(sh, im, in, ks, om, on, tw, s);
+      case 16 * 16 + 2: return dispatch_zreg_fe<8, 2>(sh, im, in, ks, om, on, tw, s);
+      case 32 * 16 + 2: return dispatch_zreg_fe<16, 2>(sh, im, in, ks, om, on, tw, s);
+      case 32 * 16 + 4: return dispatch_zreg_fe<8, 4>(sh, im, in, ks, om, on, tw, s);
+      case 64 * 16 + 4: return dispatch_zreg_fe<16, 4>(sh, im, in, ks, om, on, tw, s);
+      case 64 * 16 + 8: return dispatch_zreg_fe<8, 8>(sh, im, in, ks, om, on, tw, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (sh.pz) {
     case 16: return dispatch_z_w<16>(sh, im, in, ks, om, on, tw, s);
     case 32: return dispatch_z_w<32>(sh, im, in, ks, om, on, tw, s);

@@ -49,36 +49,35 @@ __device__ __forceinline__ double2 cmul_tw(double2 a, double2 w) {
   return make_double2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
 }
 
-// cos / sin of 2 pi k / 16, k = 0..15 (exact decimal expansions of the constants).
-__device__ __forceinline__ constexpr double c16(int k) {
-  return k == 0 ? 1.0 : k == 1 ? 0.92387953251128675613 : k == 2 ? 0.70710678118654752440
-       : k == 3 ? 0.38268343236508977173 : k == 4 ? 0.0 : k == 5 ? -0.38268343236508977173
-       : k == 6 ? -0.70710678118654752440 : k == 7 ? -0.92387953251128675613 : k == 8 ? -1.0
-       : k == 9 ? -0.92387953251128675613 : k == 10 ? -0.70710678118654752440
-       : k == 11 ? -0.38268343236508977173 : k == 12 ? 0.0 : k == 13 ? 0.38268343236508977173
-       : k == 14 ? 0.70710678118654752440 : 0.92387953251128675613;
+// cos(2 pi q / 32), q = 0..31 (decimal expansions of the constants).
+__device__ __forceinline__ constexpr double c32(int q) {
+  constexpr double t[9] = {1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
+                           0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173,
+                           0.19509032201612826785, 0.0};
+  q &= 31;
+  return q <= 8 ? t[q] : q <= 16 ? -t[16 - q] : q <= 24 ? -t[q - 16] : t[32 - q];
 }
-__device__ __forceinline__ constexpr double s16(int k) { return c16((k + 12) & 15); }
+__device__ __forceinline__ constexpr double s32(int q) { return c32(q - 8); }   // sin(a) = cos(a - pi/2)
 
-// multiply by exp(-+2 pi i k / n) for compile-time k < n <= 16, special-casing
+// multiply by exp(-+2 pi i k / n) for compile-time k < n <= 32, special-casing
 // the quarter turns so that no multiply by 0 or 1 is issued.
 template <bool INV, typename C>
 __device__ __forceinline__ C rot_const(C a, int k, int n) {
-  const int q = (16 / n) * k;     // angle index in sixteenths of a turn
+  const int q = (32 / n) * k;     // angle index in 32nds of a turn
   if (q == 0) return a;
-  if (q == 4) { C r; r.x = INV ? -a.y : a.y; r.y = INV ? a.x : -a.x; return r; }   // * (-+ i)
-  if (q == 8) { C r; r.x = -a.x; r.y = -a.y; return r; }
-  if (q == 12) { C r; r.x = INV ? a.y : -a.y; r.y = INV ? -a.x : a.x; return r; }  // * (+- i)
+  if (q == 8) { C r; r.x = INV ? -a.y : a.y; r.y = INV ? a.x : -a.x; return r; }    // * (-+ i)
+  if (q == 16) { C r; r.x = -a.x; r.y = -a.y; return r; }
+  if (q == 24) { C r; r.x = INV ? a.y : -a.y; r.y = INV ? -a.x : a.x; return r; }   // * (+- i)
   using T = decltype(a.x);
-  const T c = (T)c16(q);
-  const T s = INV ? (T)s16(q) : -(T)s16(q);
+  const T c = (T)c32(q);
+  const T s = INV ? (T)s32(q) : -(T)s32(q);
   C r;
   r.x = a.x * c - a.y * s;
   r.y = a.x * s + a.y * c;
   return r;
 }
 
-// In-register R-point DFT (R = 2, 4, 8, 16): radix-2 decimation in time written
+// In-register R-point DFT (R = 2 .. 32): radix-2 decimation in time written
 // as a template recursion, so every register index is a compile-time constant.
 template <int R, bool INV, typename C>
 struct DftReg {
@@ -116,8 +115,8 @@ template <> struct Plan<32>   { static constexpr int n = 2, r0 = 8,  r1 = 4, r2 
 template <> struct Plan<64>   { static constexpr int n = 2, r0 = 8,  r1 = 8, r2 = 1; };
 template <> struct Plan<128>  { static constexpr int n = 2, r0 = 16, r1 = 8, r2 = 1; };
 template <> struct Plan<256>  { static constexpr int n = 2, r0 = 16, r1 = 16, r2 = 1; };
-template <> struct Plan<512>  { static constexpr int n = 3, r0 = 8,  r1 = 8, r2 = 8; };
-template <> struct Plan<1024> { static constexpr int n = 3, r0 = 16, r1 = 8, r2 = 8; };
+template <> struct Plan<512>  { static constexpr int n = 2, r0 = 16, r1 = 32, r2 = 1; };
+template <> struct Plan<1024> { static constexpr int n = 2, r0 = 32, r1 = 32, r2 = 1; };
 
 // Asynchronous global -> shared copies (cp.async): every thread issues all of
 // its copies before waiting, so a whole tile is in flight at once.
@@ -141,8 +140,21 @@ __device__ __forceinline__ C tw_load(const C* tw, int idx) {
   return __ldg(tw + idx);
 }
 
+// Address of element n of line w in a tile of W lines.  With PADB > 0 every block
+// of PADB rows is shifted by W elements: the first pass writes rows R0 apart, and
+// without the shift the W-element groups of the butterflies a warp handles at once
+// land on the same shared-memory banks whenever the tile is narrower than 16 lines.
+template <int LD, int PADB, int W>
+__device__ __forceinline__ int tidx(int n, int w) {
+  return n * LD + w + (PADB > 0 ? (n / PADB) * W : 0);
+}
+template <int P, int LD, int PADB, int W>
+__host__ __device__ constexpr int tile_elems() {
+  return P * LD + (PADB > 0 ? (P / PADB) * W : 0);
+}
+
 // One Stockham pass over the tile (see file comment).
-template <int P, int R, int NS, int W, int LD, int NT, bool INV, bool ZIN, bool HOUT, typename C>
+template <int P, int R, int NS, int W, int LD, int PADB, int NT, bool INV, bool ZIN, bool HOUT, typename C>
 __device__ __forceinline__ void stockham_pass(C* buf, const C* twP, int tid) {
   constexpr int NB = (P / R) * W;
   constexpr int PER = (NB + NT - 1) / NT;
@@ -155,7 +167,7 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* twP, int tid) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (ZIN && r >= R / 2) v[q][r] = czero<C>();
-        else v[q][r] = buf[(j + r * (P / R)) * LD + w];
+        else v[q][r] = buf[tidx<LD, PADB, W>(j + r * (P / R), w)];
       }
     }
   }
@@ -177,7 +189,7 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* twP, int tid) {
       const int base = (j / NS) * NS * R + jm;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        if (!HOUT || r < R / 2) buf[(base + r * NS) * LD + w] = v[q][r];
+        if (!HOUT || r < R / 2) buf[tidx<LD, PADB, W>(base + r * NS, w)] = v[q][r];
       }
     }
   }
@@ -185,14 +197,15 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* twP, int tid) {
 }
 
 // Full length-P FFT of the W lines of a tile.  twP points at the P-table.
-template <int P, int W, int LD, int NT, bool INV, bool ZIN, bool HOUT, typename C>
+// PADB: 0 for a plain [P][LD] tile, or Plan<P>::r0 for the shifted layout (tidx).
+template <int P, int W, int LD, int NT, bool INV, bool ZIN, bool HOUT, int PADB = 0, typename C>
 __device__ __forceinline__ void fft_tile(C* buf, const C* twP, int tid) {
   using PL = Plan<P>;
-  stockham_pass<P, PL::r0, 1, W, LD, NT, INV, ZIN, (PL::n == 1) && HOUT>(buf, twP, tid);
+  stockham_pass<P, PL::r0, 1, W, LD, PADB, NT, INV, ZIN, (PL::n == 1) && HOUT>(buf, twP, tid);
   if constexpr (PL::n >= 2)
-    stockham_pass<P, PL::r1, PL::r0, W, LD, NT, INV, false, (PL::n == 2) && HOUT>(buf, twP, tid);
+    stockham_pass<P, PL::r1, PL::r0, W, LD, PADB, NT, INV, false, (PL::n == 2) && HOUT>(buf, twP, tid);
   if constexpr (PL::n >= 3)
-    stockham_pass<P, PL::r2, PL::r0 * PL::r1, W, LD, NT, INV, false, HOUT>(buf, twP, tid);
+    stockham_pass<P, PL::r2, PL::r0 * PL::r1, W, LD, PADB, NT, INV, false, HOUT>(buf, twP, tid);
 }
 
 }  // namespace dds

@@ -27,7 +27,13 @@ namespace dds {
 
 namespace {
 
-constexpr int NT = 256;
+constexpr int NT = 256;   // threads of the shared-memory z pass
+
+// Tile shapes of the x and y passes: W lines (columns) per tile, NT threads.
+// Small tiles keep several CTAs resident per SM so that one tile's copies overlap
+// another tile's transform.
+template <int P> struct XTile { static constexpr int W = 16, NT = 256; };
+template <int P> struct YTile { static constexpr int W = P >= 1024 ? 4 : (P >= 512 ? 8 : 16), NT = 128; };
 
 __device__ __forceinline__ float2 cmadd_i(float2 acc, float g, float2 r) {
   // acc + (i g) * r
@@ -37,10 +43,10 @@ __device__ __forceinline__ float2 cmadd_i(float2 acc, float g, float2 r) {
 __device__ __forceinline__ float bf16_to_f32(uint16_t v) { return __uint_as_float(((uint32_t)v) << 16); }
 
 // ---------------------------------------------------------------- x forward --
-template <int M, bool BF16>
+template <int M, int W, int NT, bool BF16>
 __global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, const void *rho_v, float2 *out_main,
                                               float2 *out_nyq, const float2 *tw) {
-  constexpr int W = 16, LD = W + 1;
+  constexpr int LD = W + 1, PB = Plan<M>::r0;
   constexpr int OWN = (W * (M / 2) + NT - 1) / NT;
   extern __shared__ float2 smem[];
   float2 *buf = smem;
@@ -64,8 +70,8 @@ __global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, const void
       const float *r = (const float *)rho_v + (long)col.fam[col.f0[g]] * N + l0 * sh.nx;
       for (int p = tid; p < W * nxh; p += NT) {
         const int w = p / nxh, n = p - w * nxh;
-        if (l0 + w < L) cp_async8(&buf[n * LD + w], r + (long)w * sh.nx + 2 * n);
-        else buf[n * LD + w] = make_float2(0.f, 0.f);
+        if (l0 + w < L) cp_async8(&buf[tidx<LD, PB, W>(n, w)], r + (long)w * sh.nx + 2 * n);
+        else buf[tidx<LD, PB, W>(n, w)] = make_float2(0.f, 0.f);
       }
     } else {
     float2 acc[OWN];
@@ -107,24 +113,24 @@ __global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, const void
       const int p = tid + i * NT;
       if (p < W * nxh) {
         const int w = p / nxh, n = p - w * nxh;
-        buf[n * LD + w] = acc[i];
+        buf[tidx<LD, PB, W>(n, w)] = acc[i];
       }
     }
     }
     for (int p = W * nxh + tid; p < W * (M / 2); p += NT) {   // zero the tail of the non-zero half
       const int w = p % W, n = p / W;
-      buf[n * LD + w] = make_float2(0.f, 0.f);
+      buf[tidx<LD, PB, W>(n, w)] = make_float2(0.f, 0.f);
     }
     cp_async_wait_all();
     __syncthreads();
-    fft_tile<M, W, LD, NT, false, true, false>(buf, twM, tid);
+    fft_tile<M, W, LD, NT, false, true, false, PB>(buf, twM, tid);
     const int e = col.e0[g] + d;
     for (int p = tid; p < W * M; p += NT) {
       const int w = p / M, k = p - w * M;
       const long line = l0 + w;
       if (line >= L) continue;
-      const float2 a = buf[k * LD + w];
-      const float2 c = buf[((M - k) & (M - 1)) * LD + w];
+      const float2 a = buf[tidx<LD, PB, W>(k, w)];
+      const float2 c = buf[tidx<LD, PB, W>((M - k) & (M - 1), w)];
       const float2 E = make_float2(0.5f * (a.x + c.x), 0.5f * (a.y - c.y));
       const float2 O = make_float2(0.5f * (a.y + c.y), -0.5f * (a.x - c.x));
       const float2 wk = __ldg(tw2 + k);
@@ -144,10 +150,10 @@ __global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, const void
 
 // ------------------------------------------------------------- y passes -----
 // Forward: rows y < ny in, all py rows out.  Inverse: all py rows in, y < ny out.
-template <int PY, int W, bool INV>
+template <int PY, int W, int NT, bool INV>
 __global__ void __launch_bounds__(NT) k_ypass(Shape sh, int nf, const float2 *in_main, const float2 *in_nyq,
                                               float2 *out_main, float2 *out_nyq, const float2 *tw) {
-  constexpr int LD = W;
+  constexpr int LD = W, PB = Plan<PY>::r0;
   extern __shared__ float2 smem[];
   float2 *buf = smem;
   const int tid = threadIdx.x;
@@ -182,24 +188,33 @@ __global__ void __launch_bounds__(NT) k_ypass(Shape sh, int nf, const float2 *in
     constexpr int H = W / 2;
     for (int p = tid; p < rows_in * H; p += NT) {
       const int n = p / H, c2 = p - n * H;
-      cp_async16(&buf[n * LD + 2 * c2], &in[n * rs + 2 * c2]);
+      cp_async16(&buf[tidx<LD, PB, W>(n, 2 * c2)], &in[n * rs + 2 * c2]);
     }
   } else {
     for (int p = tid; p < rows_in * W; p += NT) {
       const int n = p / W, w = p - n * W;
-      if (w < ncols) cp_async8(&buf[n * LD + w], &in[n * rs + w]);
-      else buf[n * LD + w] = make_float2(0.f, 0.f);
+      if (w < ncols) cp_async8(&buf[tidx<LD, PB, W>(n, w)], &in[n * rs + w]);
+      else buf[tidx<LD, PB, W>(n, w)] = make_float2(0.f, 0.f);
     }
   }
   if (!INV) {
-    for (int p = rows_in * W + tid; p < (PY / 2) * W; p += NT) buf[p] = make_float2(0.f, 0.f);
+    for (int p = rows_in * W + tid; p < (PY / 2) * W; p += NT) buf[tidx<LD, PB, W>(p / W, p % W)] = make_float2(0.f, 0.f);
   }
   cp_async_wait_all();
   __syncthreads();
-  fft_tile<PY, W, LD, NT, INV, !INV, INV>(buf, tw + tw_offset(PY), tid);
-  for (int p = tid; p < rows_out * W; p += NT) {
-    const int n = p / W, w = p - n * W;
-    if (w < ncols) out[n * rs + w] = buf[n * LD + w];
+  fft_tile<PY, W, LD, NT, INV, !INV, INV, PB>(buf, tw + tw_offset(PY), tid);
+  if (tau < tiles_main) {            // 16-byte stores of column pairs
+    constexpr int H = W / 2;
+    for (int p = tid; p < rows_out * H; p += NT) {
+      const int n = p / H, c2 = p - n * H;
+      *reinterpret_cast<float4 *>(&out[n * rs + 2 * c2]) =
+          *reinterpret_cast<const float4 *>(&buf[tidx<LD, PB, W>(n, 2 * c2)]);
+    }
+  } else {
+    for (int p = tid; p < rows_out * W; p += NT) {
+      const int n = p / W, w = p - n * W;
+      if (w < ncols) out[n * rs + w] = buf[tidx<LD, PB, W>(n, w)];
+    }
   }
 }
 
@@ -458,20 +473,20 @@ __global__ void __launch_bounds__(128) k_zreg(Shape sh, const float2 *in_main, c
 }
 
 // ---------------------------------------------------------------- x inverse --
-template <int M>
+template <int M, int W, int NT>
 __global__ void __launch_bounds__(NT) k_x_inv(Shape sh, const float2 *in_main, const float2 *in_nyq,
                                               float *sigma, const float2 *tw) {
-  constexpr int W = 16, LD = W + 1;
+  constexpr int LD = W + 1, PB = Plan<M>::r0;
   extern __shared__ float2 smem[];
   float2 *buf = smem;
-  float2 *xm = smem + M * LD;
+  float2 *xm = smem + tile_elems<M, LD, PB, W>();
   const int tid = threadIdx.x;
   const long L = 6L * sh.nz * sh.ny;
   const long l0 = (long)blockIdx.x * W;
   for (int p = tid; p < W * M; p += NT) {
     const int w = p / M, k = p - w * M;
-    if (l0 + w < L) cp_async8(&buf[k * LD + w], &in_main[(l0 + w) * M + k]);
-    else buf[k * LD + w] = make_float2(0.f, 0.f);
+    if (l0 + w < L) cp_async8(&buf[tidx<LD, PB, W>(k, w)], &in_main[(l0 + w) * M + k]);
+    else buf[tidx<LD, PB, W>(k, w)] = make_float2(0.f, 0.f);
   }
   if (tid < W) {
     const long line = l0 + tid;
@@ -490,32 +505,32 @@ __global__ void __launch_bounds__(NT) k_x_inv(Shape sh, const float2 *in_main, c
   const float2 *tw2 = tw + tw_offset(2 * M);
   for (int p = tid; p < W * (M / 2 + 1); p += NT) {
     const int w = p % W, k = p / W;
-    const float2 A = buf[k * LD + w];
-    const float2 Bm = (k == 0) ? xm[w] : buf[(M - k) * LD + w];   // X[M-k]
+    const float2 A = buf[tidx<LD, PB, W>(k, w)];
+    const float2 Bm = (k == 0) ? xm[w] : buf[tidx<LD, PB, W>(M - k, w)];   // X[M-k]
     {
       const float2 E = make_float2(A.x + Bm.x, A.y - Bm.y);
       const float2 D = make_float2(A.x - Bm.x, A.y + Bm.y);
       const float2 wk = __ldg(tw2 + k);                                  // W^k; use conj
       const float2 O = make_float2(D.x * wk.x + D.y * wk.y, D.y * wk.x - D.x * wk.y);
-      buf[k * LD + w] = make_float2(E.x - O.y, E.y + O.x);
+      buf[tidx<LD, PB, W>(k, w)] = make_float2(E.x - O.y, E.y + O.x);
     }
     if (k > 0 && k < M / 2) {
       const float2 E = make_float2(Bm.x + A.x, Bm.y - A.y);
       const float2 D = make_float2(Bm.x - A.x, Bm.y + A.y);
       const float2 wk = __ldg(tw2 + (M - k));
       const float2 O = make_float2(D.x * wk.x + D.y * wk.y, D.y * wk.x - D.x * wk.y);
-      buf[(M - k) * LD + w] = make_float2(E.x - O.y, E.y + O.x);
+      buf[tidx<LD, PB, W>(M - k, w)] = make_float2(E.x - O.y, E.y + O.x);
     }
   }
   __syncthreads();
-  fft_tile<M, W, LD, NT, true, false, true>(buf, tw + tw_offset(M), tid);
+  fft_tile<M, W, LD, NT, true, false, true, PB>(buf, tw + tw_offset(M), tid);
   const int nxh = (sh.nx + 1) >> 1;
   const bool even = (sh.nx & 1) == 0;
   for (int p = tid; p < W * nxh; p += NT) {
     const int w = p / nxh, n = p - w * nxh;
     const long line = l0 + w;
     if (line >= L) continue;
-    const float2 v = buf[n * LD + w];
+    const float2 v = buf[tidx<LD, PB, W>(n, w)];
     float *dst = sigma + line * sh.nx + 2 * n;
     if (even) {
       *reinterpret_cast<float2 *>(dst) = v;
@@ -529,7 +544,9 @@ __global__ void __launch_bounds__(NT) k_x_inv(Shape sh, const float2 *in_main, c
 // ------------------------------------------------------------ dispatch ------
 template <typename K>
 cudaError_t prep(K kernel, size_t smem) {
-  if (smem <= 48 * 1024) return cudaSuccess;
+  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+  if (err != cudaSuccess || smem <= 48 * 1024) return err;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
@@ -537,16 +554,17 @@ cudaError_t prep(K kernel, size_t smem) {
 template <int M>
 cudaError_t launch_x_fwd(const Shape &sh, const Collapse &col, const void *rho, bool bf16, float2 *om,
                          float2 *on, const float2 *tw, cudaStream_t s) {
-  const size_t smem = sizeof(float2) * M * 17;
+  constexpr int W = XTile<M>::W, T = XTile<M>::NT;
+  const size_t smem = sizeof(float2) * tile_elems<M, W + 1, Plan<M>::r0, W>();
   const long L = (long)sh.ny * sh.nz;
-  dim3 grid((unsigned)((L + 15) / 16), col.ngroups);
+  dim3 grid((unsigned)((L + W - 1) / W), col.ngroups);
   cudaError_t err;
   if (bf16) {
-    if ((err = prep(k_x_fwd<M, true>, smem)) != cudaSuccess) return err;
-    k_x_fwd<M, true><<<grid, NT, smem, s>>>(sh, col, rho, om, on, tw);
+    if ((err = prep(k_x_fwd<M, W, T, true>, smem)) != cudaSuccess) return err;
+    k_x_fwd<M, W, T, true><<<grid, T, smem, s>>>(sh, col, rho, om, on, tw);
   } else {
-    if ((err = prep(k_x_fwd<M, false>, smem)) != cudaSuccess) return err;
-    k_x_fwd<M, false><<<grid, NT, smem, s>>>(sh, col, rho, om, on, tw);
+    if ((err = prep(k_x_fwd<M, W, T, false>, smem)) != cudaSuccess) return err;
+    k_x_fwd<M, W, T, false><<<grid, T, smem, s>>>(sh, col, rho, om, on, tw);
   }
   return cudaGetLastError();
 }
@@ -554,12 +572,12 @@ cudaError_t launch_x_fwd(const Shape &sh, const Collapse &col, const void *rho, 
 template <int PY, bool INV>
 cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in, float2 *om, float2 *on,
                      const float2 *tw, cudaStream_t s) {
-  constexpr int W = PY >= 1024 ? 8 : 16;
-  const size_t smem = sizeof(float2) * PY * W;
+  constexpr int W = YTile<PY>::W, T = YTile<PY>::NT;
+  const size_t smem = sizeof(float2) * tile_elems<PY, W, Plan<PY>::r0, W>();
   const long tiles = (long)nf * sh.nz * (sh.M / W) + (long)nf * ((sh.nz + W - 1) / W);
-  cudaError_t err = prep(k_ypass<PY, W, INV>, smem);
+  cudaError_t err = prep(k_ypass<PY, W, T, INV>, smem);
   if (err != cudaSuccess) return err;
-  k_ypass<PY, W, INV><<<(unsigned)tiles, NT, smem, s>>>(sh, nf, im, in, om, on, tw);
+  k_ypass<PY, W, T, INV><<<(unsigned)tiles, T, smem, s>>>(sh, nf, im, in, om, on, tw);
   return cudaGetLastError();
 }
 
@@ -577,11 +595,12 @@ cudaError_t launch_z(const Shape &sh, const float2 *im, const float2 *in, const 
 template <int M>
 cudaError_t launch_x_inv(const Shape &sh, const float2 *im, const float2 *in, float *sigma, const float2 *tw,
                          cudaStream_t s) {
-  const size_t smem = sizeof(float2) * (M * 17 + 16);
+  constexpr int W = XTile<M>::W, T = XTile<M>::NT;
+  const size_t smem = sizeof(float2) * (tile_elems<M, W + 1, Plan<M>::r0, W>() + W);
   const long L = 6L * sh.nz * sh.ny;
-  cudaError_t err = prep(k_x_inv<M>, smem);
+  cudaError_t err = prep(k_x_inv<M, W, T>, smem);
   if (err != cudaSuccess) return err;
-  k_x_inv<M><<<(unsigned)((L + 15) / 16), NT, smem, s>>>(sh, im, in, sigma, tw);
+  k_x_inv<M, W, T><<<(unsigned)((L + W - 1) / W), T, smem, s>>>(sh, im, in, sigma, tw);
   return cudaGetLastError();
 }
 

@@ -114,6 +114,28 @@ int dds_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, void 
 int dds_stress_batched(dds_ctx **ctxs, int n, const void **rho, const int *rho_dtype,
                        float **sigma, void *cuda_stream);
 
+/* Size of the fixed device work area used by dds_stress_noalloc (32 MiB). */
+#define DDS_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Evaluation that allocates nothing.  The paper has no counterpart: this is an
+ * interface for callers that cannot call cudaMalloc while they run -- for example
+ * code whose device memory is wholly owned by another allocator (a framework's
+ * caching pool that must account for every byte) or a loop that may not allocate
+ * once it has started.  Same inputs, outputs and result as dds_stress (the context
+ * must be built by dds_build_kernels during set-up), but the work buffers between
+ * the passes come from one fixed area of DDS_NOALLOC_SCRATCH_BYTES that the library
+ * declares as device memory; every GPU that loads the library holds that area until
+ * the process exits.  The first call on a device looks up the area's device address
+ * (cudaGetSymbolAddress, once per device); make that first call before any stream
+ * capture.  All calls, from any context or stream, share the one area and its
+ * contents persist between calls: calls whose executions overlap on the GPU race,
+ * so serialise them (one stream, or events).  No part of the area needs to start at
+ * zero: every element a pass reads was written earlier in the same call.  Grids
+ * whose work space exceeds the area (about 64x64x32 cells with 4 combined fields
+ * fits) are rejected with DDS_ERR_UNSUPPORTED and a message giving the size
+ * needed.  Enqueued on `cuda_stream`; returns without synchronising. */
+int dds_stress_noalloc(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, void *cuda_stream);
+
 /* End-to-end variant with HOST buffers: copies rho_host (float32, [F][nz][ny][nx])
  * to the device, evaluates, copies sigma back to sigma_host (float32,
  * [6][nz][ny][nx]) and synchronises the stream.  Device staging buffers are owned

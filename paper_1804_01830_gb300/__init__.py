@@ -31,7 +31,7 @@ DDS_OPT_Z_LANES = 2
 
 # Every symbol include/dds.h declares.
 EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option",
-           "dds_build_kernels", "dds_stress", "dds_stress_batched", "dds_stress_host",
+           "dds_build_kernels", "dds_stress", "dds_stress_batched", "dds_stress_noalloc", "dds_stress_host",
            "dds_table_at", "dds_query", "dds_launches_per_stress", "dds_profile_enable",
            "dds_profile_read", "dds_last_error", "dds_destroy")
 
@@ -65,6 +65,7 @@ def load_library():
         "dds_stress": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
         "dds_stress_batched": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), ip,
                                 ctypes.POINTER(vp), vp], ctypes.c_int),
+        "dds_stress_noalloc": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
         "dds_stress_host": ([vp, vp, vp, vp], ctypes.c_int),
         "dds_table_at": ([vp, dp, dp, lp, ip, dp], ctypes.c_int),
         "dds_query": ([vp, ip, ip, ip, ip], ctypes.c_int),
@@ -140,6 +141,12 @@ def dds_stress_batched(ctxs, rho_ptrs, rho_dtypes, sigma_ptrs, stream=None):
     arr_s = (ctypes.c_void_p * n)(*sigma_ptrs)
     rc = load_library().dds_stress_batched(arr_c, n, arr_r, arr_d, arr_s, _stream_handle(stream))
     _check(ctxs[0] if n else None, rc)
+
+
+def dds_stress_noalloc(ctx, rho_ptr: int, rho_dtype: int, sigma_ptr: int, stream=None):
+    """dds_stress with its work buffers in the library's fixed device area (no allocation)."""
+    _check(ctx, load_library().dds_stress_noalloc(ctx, ctypes.c_void_p(rho_ptr), int(rho_dtype),
+                                                  ctypes.c_void_p(sigma_ptr), _stream_handle(stream)))
 
 
 def dds_stress_host(ctx, rho_host: np.ndarray, sigma_host: np.ndarray, stream=None):

@@ -109,6 +109,8 @@ int build_spectra(dds_ctx *ctx, cudaStream_t s);
 // Enqueue one stress evaluation.
 int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s);
 int stress_launch_count(const Shape &sh);
+int enqueue_stress_buffers(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, float2 *bufA, float2 *bufB,
+                           float2 *nyqA, float2 *nyqB, cudaStream_t s);
 
 // Set ctx->err (printf-style) and return code.
 int fail(dds_ctx *ctx, int code, const char *fmt, ...);

@@ -745,4 +745,18 @@ int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, c
   return DDS_OK;
 }
 
+// The five passes on caller-provided work buffers (used by dds_stress_noalloc).
+int enqueue_stress_buffers(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, float2 *bufA, float2 *bufB,
+                           float2 *nyqA, float2 *nyqB, cudaStream_t s) {
+  const Shape &sh = ctx->shape;
+  const float2 *tw = ctx->tw.f32;
+  cudaError_t err = dispatch_x_fwd(sh, ctx->col, rho, rho_dtype == DDS_BF16, bufA, nyqA, tw, s);
+  if (err == cudaSuccess) err = dispatch_y<false>(sh, sh.fe, bufA, nyqA, bufB, nyqB, tw, s);
+  if (err == cudaSuccess) err = dispatch_z(sh, bufB, nyqB, ctx->kspec, bufA, nyqA, tw, s);
+  if (err == cudaSuccess) err = dispatch_y<true>(sh, 6, bufA, nyqA, bufB, nyqB, tw, s);
+  if (err == cudaSuccess) err = dispatch_x_inv(sh, bufB, nyqB, sigma, tw, s);
+  if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress: kernel launch failed: %s", cudaGetErrorString(err));
+  return DDS_OK;
+}
+
 }  // namespace dds

@@ -41,7 +41,7 @@ PASS_NAMES = ("x_fwd", "y_fwd", "z_fused", "y_inv", "x_inv")
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.CONFIGS))
@@ -81,7 +81,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
@@ -153,13 +153,21 @@ def measured_peaks():
         return {}
 
 
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("paper_1804_01830_gb300/csrc/stress.cu", "paper_1804_01830_gb300/csrc/dds_fft.cuh"):
+        h.update((ROOT / f).read_bytes())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if current."""
+    """DRAM bytes per launch of `kernel` from the committed ncu record, or None when the
+    kernel sources changed since those counters were taken."""
     f = ROOT / "profiles" / "ncu_traffic.json"
     try:
-        d = json.loads(f.read_text())
-        e = d[workload][kernel]
-        return float(e["dram_bytes_per_launch"]) if e.get("current", False) else None
+        e = json.loads(f.read_text())[workload][kernel]
+        return float(e["dram_bytes_per_launch"]) if e["source_hash"] == kernel_source_hash() else None
     except Exception:
         return None
 

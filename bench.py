@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true", help="skip the cuFFT comparator")
     return ap.parse_args()
 
 
@@ -170,6 +171,63 @@ def ncu_traffic(kernel: str, workload: str):
         return float(e["dram_bytes_per_launch"]) if e["source_hash"] == kernel_source_hash() else None
     except Exception:
         return None
+
+
+# -------------------------------------------------------- cuFFT comparator --
+def cufft_comparator(p, q, steps: int = 20, warmup: int = 3):
+    """The same convolution with cuFFT (torch.fft) on the full zero-padded grid and a
+    separate contraction: pad rho, R2C of every field, sigma^_c = sum_e i g_ce rho^_e
+    (FP32 imaginary-only spectra, as in our path; values are random -- timing only),
+    C2R of the six components, crop.  Returns ms per evaluation for the whole
+    comparator and for its FFTs alone (a lower bound for any cuFFT-based pipeline)."""
+    import torch
+    g = p.geom
+    nz, ny, nx = g.nz, g.ny, g.nx
+    pz, py, px = q["pz"], q["py"], q["px"]
+    fe = q["n_fields"]
+    dev = "cuda"
+    rho = torch.rand((fe, nz, ny, nx), device=dev)
+    pad = torch.zeros((fe, pz, py, px), device=dev)
+    kx = px // 2 + 1
+    gspec = torch.rand((6, fe, pz, py, kx), device=dev)
+    sig = torch.empty((6, nz, ny, nx), device=dev)
+
+    def full():
+        pad[:, :nz, :ny, :nx].copy_(rho)
+        R = torch.fft.rfftn(pad, dim=(1, 2, 3))
+        Rr = torch.view_as_real(R)                      # (fe, pz, py, kx, 2)
+        S = torch.zeros((6, pz, py, kx), dtype=torch.complex64, device=dev)
+        Sr = torch.view_as_real(S)
+        for c in range(6):                              # sigma^_c = sum_e i g_ce rho^_e
+            for e in range(fe):
+                Sr[c, ..., 0].addcmul_(gspec[c, e], Rr[e, ..., 1], value=-1.0)
+                Sr[c, ..., 1].addcmul_(gspec[c, e], Rr[e, ..., 0])
+        out = torch.fft.irfftn(S, s=(pz, py, px), dim=(1, 2, 3))
+        sig.copy_(out[:, :nz, :ny, :nx])
+
+    spec_out = torch.empty((6, pz, py, kx), dtype=torch.complex64, device=dev)
+
+    def fft_only():
+        pad[:, :nz, :ny, :nx].copy_(rho)
+        torch.fft.rfftn(pad, dim=(1, 2, 3))
+        out = torch.fft.irfftn(spec_out, s=(pz, py, px), dim=(1, 2, 3))
+        sig.copy_(out[:, :nz, :ny, :nx])
+
+    res = {}
+    for name, fn in (("cufft_plus_contraction_ms", full), ("cufft_ffts_only_ms", fft_only)):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = a.elapsed_time(b) / steps
+    del pad, gspec, rho, sig, spec_out
+    torch.cuda.empty_cache()
+    return res
 
 
 # ----------------------------------------------------------- CPU baseline --
@@ -310,6 +368,12 @@ def run_ours(args):
                "h2d_bytes_per_step": int(rho_h.numel() * 4), "d2h_bytes_per_step": int(sig_h.numel() * 4),
                "steps": ke}
 
+    comparator = None
+    if not args.no_comparator:
+        comparator = cufft_comparator(p, q)
+        comparator["ours_ms"] = total_ms / K
+        comparator["speedup_vs_cufft_plus_contraction"] = comparator["cufft_plus_contraction_ms"] / (total_ms / K)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt, cores = oracle_sample(p, args.cpu_seconds)
@@ -333,6 +397,7 @@ def run_ours(args):
         "step_roofline": {"bytes_pass_model": step_bytes, "bytes_floor": floor_bytes(p, q),
                           "frac_pass_model": step_bytes / (total_ms / K * 1e-3) / 1e9 / peak},
         "e2e": e2e,
+        "gpu_comparator": comparator,
         "cpu_baseline": cpu,
         "gpu_launches": K * ctx.launches_per_stress,
         "clocks": clk,

@@ -221,13 +221,14 @@ int make_plan(dds_ctx *ctx) {
     if (ctx->z_lanes > 0)
       return fail(ctx, DDS_ERR_UNSUPPORTED, "z pass: %d lanes per column not available for pz %d", G, sh.pz);
   }
+  // shared-memory z pass: fe field lines and three component lines per column
   const size_t pref = 110 * 1024, cap = 220 * 1024;
   for (int pass = 0; pass < 2 && sh.wz == 0; ++pass) {
     for (int W : {64, 32, 16, 8, 4}) {
       if (W > sh.M || sh.py % W != 0) continue;
       if (W * sh.pz > 2048 && W > 8) continue;
       const size_t fe = (size_t)std::max(sh.fe, 1);
-      const size_t smem = (sizeof(float2) * (fe + 1) + sizeof(float) * fe) * sh.pz * W;
+      const size_t smem = (sizeof(float2) * (fe + 3) + 2 * sizeof(float) * fe) * sh.pz * W;
       if (smem <= (pass == 0 ? pref : cap)) { sh.wz = W; break; }
     }
   }
@@ -508,7 +509,7 @@ int dds_query(const dds_ctx *ctx, int *n_fields, int *px, int *py, int *pz) {
 
 int dds_launches_per_stress(const dds_ctx *ctx) {
   if (!ctx || !ctx->built) return 0;
-  return ctx->fe == 0 ? 0 : stress_launch_count(ctx->shape);
+  return ctx->fe == 0 ? 0 : stress_launch_count(ctx->shape, ctx->col);
 }
 
 int dds_profile_enable(dds_ctx *ctx, int enable) {

@@ -129,6 +129,10 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N committed groups of this thread are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Twiddle tables: for every power of two P in [16, 2048] the values
 // exp(-2 pi i k / P), k = 0..P-1, stored back to back starting at offset P - 16.
@@ -206,6 +210,57 @@ __device__ __forceinline__ void fft_tile(C* buf, const C* twP, int tid) {
     stockham_pass<P, PL::r1, PL::r0, W, LD, PADB, NT, INV, false, (PL::n == 2) && HOUT>(buf, twP, tid);
   if constexpr (PL::n >= 3)
     stockham_pass<P, PL::r2, PL::r0 * PL::r1, W, LD, PADB, NT, INV, false, HOUT>(buf, twP, tid);
+}
+
+// Variant with a runtime number of interleaved lines L <= LMAX (row pitch L):
+// lets one pass transform several fields (or components) of a tile together.
+template <int P, int R, int NS, int LMAX, int NT, bool INV, bool ZIN, bool HOUT, typename C>
+__device__ __forceinline__ void stockham_pass_rt(C* buf, int L, const C* twP, int tid) {
+  constexpr int PER = ((P / R) * LMAX + NT - 1) / NT;
+  const int NB = (P / R) * L;
+  C v[PER][R];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int bi = tid + q * NT;
+    if (bi < NB) {
+      const int j = bi / L, w = bi - j * L;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (ZIN && r >= R / 2) v[q][r] = czero<C>();
+        else v[q][r] = buf[(j + r * (P / R)) * L + w];
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int bi = tid + q * NT;
+    if (bi < NB) {
+      const int j = bi / L, w = bi - j * L;
+      const int jm = j % NS;
+      if (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[q][r] = cmul_tw<INV>(v[q][r], tw_load(twP, jm * r * (P / (NS * R))));
+      }
+      dft_reg<R, INV>(v[q]);
+      const int base = (j / NS) * NS * R + jm;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!HOUT || r < R / 2) buf[(base + r * NS) * L + w] = v[q][r];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int P, int LMAX, int NT, bool INV, bool ZIN, bool HOUT, typename C>
+__device__ __forceinline__ void fft_tile_rt(C* buf, int L, const C* twP, int tid) {
+  using PL = Plan<P>;
+  stockham_pass_rt<P, PL::r0, 1, LMAX, NT, INV, ZIN, (PL::n == 1) && HOUT>(buf, L, twP, tid);
+  if constexpr (PL::n >= 2)
+    stockham_pass_rt<P, PL::r1, PL::r0, LMAX, NT, INV, false, (PL::n == 2) && HOUT>(buf, L, twP, tid);
+  if constexpr (PL::n >= 3)
+    stockham_pass_rt<P, PL::r2, PL::r0 * PL::r1, LMAX, NT, INV, false, HOUT>(buf, L, twP, tid);
 }
 
 }  // namespace dds

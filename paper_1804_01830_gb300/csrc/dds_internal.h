@@ -22,6 +22,12 @@ struct Collapse {
   float coef[DDS_MAX_FAMILIES][3];
 };
 
+// Subset of groups handled by one launch of the x forward pass.
+struct GroupList {
+  int n;
+  int g[MAX_GROUPS];
+};
+
 // Geometry of one evaluation as the device kernels see it.
 struct Shape {
   int nx, ny, nz;     // grid
@@ -108,7 +114,7 @@ int build_spectra(dds_ctx *ctx, cudaStream_t s);
 
 // Enqueue one stress evaluation.
 int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s);
-int stress_launch_count(const Shape &sh);
+int stress_launch_count(const Shape &sh, const Collapse &col);
 int enqueue_stress_buffers(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, float2 *bufA, float2 *bufB,
                            float2 *nyqA, float2 *nyqB, cudaStream_t s);
 

@@ -43,9 +43,9 @@ __device__ __forceinline__ float2 cmadd_i(float2 acc, float g, float2 r) {
 __device__ __forceinline__ float bf16_to_f32(uint16_t v) { return __uint_as_float(((uint32_t)v) << 16); }
 
 // ---------------------------------------------------------------- x forward --
-template <int M, int W, int NT, bool BF16>
-__global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, const void *rho_v, float2 *out_main,
-                                              float2 *out_nyq, const float2 *tw) {
+template <int M, int W, int NT, bool BF16, bool DIRECT>
+__global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, GroupList gl, const void *rho_v,
+                                              float2 *out_main, float2 *out_nyq, const float2 *tw) {
   constexpr int LD = W + 1, PB = Plan<M>::r0;
   constexpr int OWN = (W * (M / 2) + NT - 1) / NT;
   extern __shared__ float2 smem[];
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, const void
   const long L = (long)sh.ny * sh.nz;
   const long N = L * sh.nx;
   const long l0 = (long)blockIdx.x * W;
-  const int g = blockIdx.y;
+  const int g = gl.g[blockIdx.y];
   const int nxh = (sh.nx + 1) >> 1;
   const bool even = (sh.nx & 1) == 0;
   const float2 *twM = tw + tw_offset(M);
@@ -62,10 +62,58 @@ __global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, const void
 
   // A group with one family (coefficient c) needs no combination: its line pairs are
   // copied straight into the transposed tile and the spectrum is scaled by c.
-  const bool direct = !BF16 && even && col.nf[g] == 1 && col.nd[g] == 1;
-  for (int d = 0; d < col.nd[g]; ++d) {
+  // Otherwise every family of the group is read once and accumulated into all of
+  // the group's fields (at most three) in registers.
+  const int nd = col.nd[g];
+  float2 acc[DIRECT ? 1 : 3][OWN];
+  if constexpr (!DIRECT) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int i = 0; i < OWN; ++i) acc[d][i] = make_float2(0.f, 0.f);
+    for (int q = 0; q < col.nf[g]; ++q) {
+      const float c0 = col.coef[col.f0[g] + q][0], c1 = col.coef[col.f0[g] + q][1],
+                  c2 = col.coef[col.f0[g] + q][2];
+      const long fbase = (long)col.fam[col.f0[g] + q] * N + l0 * sh.nx;
+      float2 v[OWN];
+#pragma unroll
+      for (int i = 0; i < OWN; ++i) {
+        v[i] = make_float2(0.f, 0.f);
+        const int p = tid + i * NT;
+        if (p < W * nxh) {
+          const int w = p / nxh, n = p - w * nxh;
+          if (l0 + w < L) {
+            const long o = fbase + (long)w * sh.nx + 2 * n;
+            if (BF16) {
+              const uint16_t *r = (const uint16_t *)rho_v;
+              v[i].x = bf16_to_f32(r[o]);
+              v[i].y = (2 * n + 1 < sh.nx) ? bf16_to_f32(r[o + 1]) : 0.f;
+            } else {
+              const float *r = (const float *)rho_v;
+              if (even) {
+                v[i] = *reinterpret_cast<const float2 *>(r + o);
+              } else {
+                v[i].x = r[o];
+                v[i].y = (2 * n + 1 < sh.nx) ? r[o + 1] : 0.f;
+              }
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < OWN; ++i) {
+        acc[0][i].x = fmaf(c0, v[i].x, acc[0][i].x);
+        acc[0][i].y = fmaf(c0, v[i].y, acc[0][i].y);
+        acc[1][i].x = fmaf(c1, v[i].x, acc[1][i].x);
+        acc[1][i].y = fmaf(c1, v[i].y, acc[1][i].y);
+        acc[2][i].x = fmaf(c2, v[i].x, acc[2][i].x);
+        acc[2][i].y = fmaf(c2, v[i].y, acc[2][i].y);
+      }
+    }
+  }
+  for (int d = 0; d < nd; ++d) {
     float scale_out = 1.0f;
-    if (direct) {
+    if constexpr (DIRECT) {
       scale_out = col.coef[col.f0[g]][0];
       const float *r = (const float *)rho_v + (long)col.fam[col.f0[g]] * N + l0 * sh.nx;
       for (int p = tid; p < W * nxh; p += NT) {
@@ -74,48 +122,14 @@ __global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, const void
         else buf[tidx<LD, PB, W>(n, w)] = make_float2(0.f, 0.f);
       }
     } else {
-    float2 acc[OWN];
-#pragma unroll
-    for (int i = 0; i < OWN; ++i) acc[i] = make_float2(0.f, 0.f);
-    for (int q = 0; q < col.nf[g]; ++q) {
-      const float cf = col.coef[col.f0[g] + q][d];
-      if (cf == 0.f) continue;
-      const long fbase = (long)col.fam[col.f0[g] + q] * N + l0 * sh.nx;
 #pragma unroll
       for (int i = 0; i < OWN; ++i) {
         const int p = tid + i * NT;
         if (p < W * nxh) {
           const int w = p / nxh, n = p - w * nxh;
-          if (l0 + w < L) {
-            const long o = fbase + (long)w * sh.nx + 2 * n;
-            float2 v;
-            if (BF16) {
-              const uint16_t *r = (const uint16_t *)rho_v;
-              v.x = bf16_to_f32(r[o]);
-              v.y = (2 * n + 1 < sh.nx) ? bf16_to_f32(r[o + 1]) : 0.f;
-            } else {
-              const float *r = (const float *)rho_v;
-              if (even) {
-                v = *reinterpret_cast<const float2 *>(r + o);
-              } else {
-                v.x = r[o];
-                v.y = (2 * n + 1 < sh.nx) ? r[o + 1] : 0.f;
-              }
-            }
-            acc[i].x = fmaf(cf, v.x, acc[i].x);
-            acc[i].y = fmaf(cf, v.y, acc[i].y);
-          }
+          if constexpr (!DIRECT) buf[tidx<LD, PB, W>(n, w)] = d == 0 ? acc[0][i] : (d == 1 ? acc[1][i] : acc[2][i]);
         }
       }
-    }
-#pragma unroll
-    for (int i = 0; i < OWN; ++i) {
-      const int p = tid + i * NT;
-      if (p < W * nxh) {
-        const int w = p / nxh, n = p - w * nxh;
-        buf[tidx<LD, PB, W>(n, w)] = acc[i];
-      }
-    }
     }
     for (int p = W * nxh + tid; p < W * (M / 2); p += NT) {   // zero the tail of the non-zero half
       const int w = p % W, n = p / W;
@@ -219,20 +233,26 @@ __global__ void __launch_bounds__(NT) k_ypass(Shape sh, int nf, const float2 *in
 }
 
 // ------------------------------------------------------------- fused z ------
-// Shared memory: fe field tiles [PZ][W], one output tile [PZ][W], and the kernel
-// spectra of one stress component for this tile [fe][PZ][W] (FP32).  The spectra
-// of component c+1 stream in (cp.async) while component c is inverted and stored.
-template <int PZ, int W>
+// Shared-memory variant for tall grids (or many fields).  A tile is W adjacent
+// columns.  The fields are interleaved in one tile F[z][e W + w] and transformed
+// together (fe W lines).  The kernel spectra of one component for the tile
+// (fe x PZ x W values) stream into one of two buffers G by cp.async while the
+// previous component is contracted, and while the inverse FFTs run; the six
+// components are formed in S[z][c' W + w] and inverted three at a time.
+template <int PZ, int W, int FEMAX>
 __global__ void __launch_bounds__(NT) k_zpass(Shape sh, const float2 *in_main, const float2 *in_nyq,
                                               const float *kspec, float2 *out_main, float2 *out_nyq,
                                               const float2 *tw) {
-  constexpr int LD = W, TS = PZ * W;
+  constexpr int TS = PZ * W;                 // positions of one field in the tile
+  constexpr int LF = FEMAX * W;              // most field lines
   extern __shared__ float2 smem[];
   const int tid = threadIdx.x;
   const int M = sh.M, py = sh.py, nz = sh.nz, fe = sh.fe;
-  float2 *fields = smem;            // [fe][PZ][W]
-  float2 *obuf = smem + (long)fe * TS;
-  float *gbuf = reinterpret_cast<float *>(obuf + TS);   // [fe][PZ][W]
+  const int L = fe * W;
+  float2 *F = smem;                                       // [PZ][fe W]
+  float2 *S = smem + (long)PZ * L;                        // [PZ][3 W]
+  float *G0 = reinterpret_cast<float *>(S + 3 * TS);      // [fe][PZ][W], two buffers
+  float *G1 = G0 + (long)fe * TS;
   const long ktiles = M / W;
   const long tiles_main = (long)py * ktiles;
   const long tau = blockIdx.x;
@@ -245,68 +265,56 @@ __global__ void __launch_bounds__(NT) k_zpass(Shape sh, const float2 *in_main, c
     ky0 = (tau - tiles_main) * W;
   }
   const float *ks = kspec + tau * 6L * fe * TS;
-  const int gchunks = fe * TS / 4;   // 16-byte chunks of one component's spectra
-  // rows z < nz of every field, and the spectra of component 0
-  for (int e = 0; e < fe; ++e) {
-    float2 *f = fields + (long)e * TS;
-    if (!nyq) {
-      constexpr int H = W / 2;
-      const float2 *src = in_main + ((long)e * nz * py + ky) * M + kx0;
-      for (int p = tid; p < nz * H; p += NT) {
-        const int z = p / H, c2 = p - z * H;
-        cp_async16(&f[z * LD + 2 * c2], &src[(long)z * py * M + 2 * c2]);
-      }
-    } else {
-      const float2 *src = in_nyq + ((long)e * py + ky0) * nz;
-      for (int p = tid; p < nz * W; p += NT) {
-        const int w = p / nz, z = p - w * nz;
-        cp_async8(&f[z * LD + w], &src[(long)w * nz + z]);
-      }
+  const int gchunks = fe * TS / 4;                        // 16-byte chunks of one component
+  auto load_spectra = [&](int c, float *dst) {
+    const float *src = ks + (long)c * fe * TS;
+    for (int q = tid; q < gchunks; q += NT) cp_async16(dst + 4 * q, src + 4 * q);
+    cp_async_commit();
+  };
+  // rows z < nz of every field; rows [nz, PZ/2) zero
+  if (!nyq) {
+    constexpr int H = W / 2;
+    for (int p = tid; p < nz * fe * H; p += NT) {
+      const int z = p / (fe * H), r = p - z * (fe * H), e = r / H, c2 = r - e * H;
+      cp_async16(&F[z * L + e * W + 2 * c2], in_main + (((long)e * nz + z) * py + ky) * M + kx0 + 2 * c2);
     }
-    for (int p = nz * W + tid; p < (PZ / 2) * W; p += NT) f[p] = make_float2(0.f, 0.f);
+  } else {
+    for (int p = tid; p < nz * fe * W; p += NT) {
+      const int e = p / (nz * W), r = p - e * (nz * W), w = r / nz, z = r - w * nz;
+      cp_async8(&F[z * L + e * W + w], in_nyq + ((long)e * py + ky0 + w) * nz + z);
+    }
   }
-  for (int q = tid; q < gchunks; q += NT) cp_async16(gbuf + 4 * q, ks + 4 * q);
-  cp_async_wait_all();
+  cp_async_commit();
+  load_spectra(0, G0);
+  for (int p = nz * L + tid; p < (PZ / 2) * L; p += NT) F[p] = make_float2(0.f, 0.f);
+  cp_async_wait_group<1>();                               // fields have landed
   __syncthreads();
   const float2 *twP = tw + tw_offset(PZ);
-  for (int e = 0; e < fe; ++e) fft_tile<PZ, W, LD, NT, false, true, false>(fields + (long)e * TS, twP, tid);
+  fft_tile_rt<PZ, LF, NT, false, true, false>(F, L, twP, tid);
 
   for (int c = 0; c < 6; ++c) {
-    for (int q = tid; q < TS / 4; q += NT) {          // four consecutive positions per thread
-      float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
-      for (int e = 0; e < fe; ++e) {
-        const float4 g = *reinterpret_cast<const float4 *>(gbuf + (long)e * TS + 4 * q);
-        const float4 r01 = *reinterpret_cast<const float4 *>(fields + (long)e * TS + 4 * q);
-        const float4 r23 = *reinterpret_cast<const float4 *>(fields + (long)e * TS + 4 * q + 2);
-        a0 = cmadd_i(a0, g.x, make_float2(r01.x, r01.y));
-        a1 = cmadd_i(a1, g.y, make_float2(r01.z, r01.w));
-        a2 = cmadd_i(a2, g.z, make_float2(r23.x, r23.y));
-        a3 = cmadd_i(a3, g.w, make_float2(r23.z, r23.w));
-      }
-      *reinterpret_cast<float4 *>(obuf + 4 * q) = make_float4(a0.x, a0.y, a1.x, a1.y);
-      *reinterpret_cast<float4 *>(obuf + 4 * q + 2) = make_float4(a2.x, a2.y, a3.x, a3.y);
-    }
+    float *Gc = (c & 1) ? G1 : G0;
+    cp_async_wait_group<0>();                             // spectra of component c
     __syncthreads();
-    if (c < 5) {
-      const float *kn = ks + (long)(c + 1) * fe * TS;
-      for (int q = tid; q < gchunks; q += NT) cp_async16(gbuf + 4 * q, kn + 4 * q);
+    if (c < 5) load_spectra(c + 1, (c & 1) ? G0 : G1);    // next component flies meanwhile
+    const int c3 = c % 3;
+    for (int p = tid; p < TS; p += NT) {                  // position p = kz W + w
+      const int kz = p / W, w = p - kz * W;
+      float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int e = 0; e < FEMAX; ++e)
+        if (e < fe) a = cmadd_i(a, Gc[(long)e * TS + p], F[kz * L + e * W + w]);
+      S[kz * (3 * W) + c3 * W + w] = a;
     }
-    fft_tile<PZ, W, LD, NT, true, false, true>(obuf, twP, tid);
-    if (!nyq) {
-      float2 *dst = out_main + ((long)c * nz * py + ky) * M + kx0;
-      for (int p = tid; p < nz * W; p += NT) {
-        const int z = p / W, w = p - z * W;
-        dst[(long)z * py * M + w] = obuf[z * LD + w];
-      }
-    } else {
-      float2 *dst = out_nyq + ((long)c * py + ky0) * nz;
-      for (int p = tid; p < nz * W; p += NT) {
-        const int w = p / nz, z = p - w * nz;
-        dst[(long)w * nz + z] = obuf[z * LD + w];
+    if (c3 == 2) {
+      __syncthreads();
+      fft_tile_rt<PZ, 3 * W, NT, true, false, true>(S, 3 * W, twP, tid);
+      for (int p = tid; p < nz * 3 * W; p += NT) {
+        const int z = p / (3 * W), r = p - z * (3 * W), cc = c - 2 + r / W, w = r % W;
+        if (!nyq) out_main[(((long)cc * nz + z) * py + ky) * M + kx0 + w] = S[p];
+        else out_nyq[((long)cc * py + ky0 + w) * nz + z] = S[p];
       }
     }
-    cp_async_wait_all();
-    __syncthreads();
   }
 }
 
@@ -551,22 +559,38 @@ cudaError_t prep(K kernel, size_t smem) {
 }
 
 
-template <int M>
-cudaError_t launch_x_fwd(const Shape &sh, const Collapse &col, const void *rho, bool bf16, float2 *om,
-                         float2 *on, const float2 *tw, cudaStream_t s) {
+template <int M, bool BF16, bool DIRECT>
+cudaError_t launch_x_fwd_kind(const Shape &sh, const Collapse &col, const GroupList &gl, const void *rho,
+                              float2 *om, float2 *on, const float2 *tw, cudaStream_t s) {
   constexpr int W = XTile<M>::W, T = XTile<M>::NT;
   const size_t smem = sizeof(float2) * tile_elems<M, W + 1, Plan<M>::r0, W>();
   const long L = (long)sh.ny * sh.nz;
-  dim3 grid((unsigned)((L + W - 1) / W), col.ngroups);
-  cudaError_t err;
-  if (bf16) {
-    if ((err = prep(k_x_fwd<M, W, T, true>, smem)) != cudaSuccess) return err;
-    k_x_fwd<M, W, T, true><<<grid, T, smem, s>>>(sh, col, rho, om, on, tw);
-  } else {
-    if ((err = prep(k_x_fwd<M, W, T, false>, smem)) != cudaSuccess) return err;
-    k_x_fwd<M, W, T, false><<<grid, T, smem, s>>>(sh, col, rho, om, on, tw);
-  }
+  dim3 grid((unsigned)((L + W - 1) / W), gl.n);
+  cudaError_t err = prep(k_x_fwd<M, W, T, BF16, DIRECT>, smem);
+  if (err != cudaSuccess) return err;
+  k_x_fwd<M, W, T, BF16, DIRECT><<<grid, T, smem, s>>>(sh, col, gl, rho, om, on, tw);
   return cudaGetLastError();
+}
+
+// Groups with one family read that family straight into the tile (single-family
+// kernel); the others accumulate their families in registers.
+template <int M>
+cudaError_t launch_x_fwd(const Shape &sh, const Collapse &col, const void *rho, bool bf16, float2 *om,
+                         float2 *on, const float2 *tw, cudaStream_t s) {
+  GroupList direct{}, accum{};
+  for (int g = 0; g < col.ngroups; ++g) {
+    const bool d = !bf16 && (sh.nx % 2 == 0) && col.nf[g] == 1 && col.nd[g] == 1;
+    if (col.nd[g] == 0) continue;
+    GroupList &gl = d ? direct : accum;
+    gl.g[gl.n++] = g;
+  }
+  cudaError_t err = cudaSuccess;
+  if (direct.n > 0) err = launch_x_fwd_kind<M, false, true>(sh, col, direct, rho, om, on, tw, s);
+  if (err == cudaSuccess && accum.n > 0) {
+    err = bf16 ? launch_x_fwd_kind<M, true, false>(sh, col, accum, rho, om, on, tw, s)
+               : launch_x_fwd_kind<M, false, false>(sh, col, accum, rho, om, on, tw, s);
+  }
+  return err;
 }
 
 template <int PY, bool INV>
@@ -581,15 +605,22 @@ cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in
   return cudaGetLastError();
 }
 
+template <int PZ, int W, int FEMAX>
+cudaError_t launch_z_fe(const Shape &sh, const float2 *im, const float2 *in, const float *ks, float2 *om,
+                        float2 *on, const float2 *tw, cudaStream_t s) {
+  const size_t smem = (sizeof(float2) * (size_t)(sh.fe + 3) + 2 * sizeof(float) * (size_t)sh.fe) * PZ * W;
+  const long tiles = (long)sh.py * (sh.M / W) + sh.py / W;
+  cudaError_t err = prep(k_zpass<PZ, W, FEMAX>, smem);
+  if (err != cudaSuccess) return err;
+  k_zpass<PZ, W, FEMAX><<<(unsigned)tiles, NT, smem, s>>>(sh, im, in, ks, om, on, tw);
+  return cudaGetLastError();
+}
+
 template <int PZ, int W>
 cudaError_t launch_z(const Shape &sh, const float2 *im, const float2 *in, const float *ks, float2 *om,
                      float2 *on, const float2 *tw, cudaStream_t s) {
-  const size_t smem = (sizeof(float2) * (size_t)(sh.fe + 1) + sizeof(float) * (size_t)sh.fe) * PZ * W;
-  const long tiles = (long)sh.py * (sh.M / W) + sh.py / W;
-  cudaError_t err = prep(k_zpass<PZ, W>, smem);
-  if (err != cudaSuccess) return err;
-  k_zpass<PZ, W><<<(unsigned)tiles, NT, smem, s>>>(sh, im, in, ks, om, on, tw);
-  return cudaGetLastError();
+  if (sh.fe <= 6) return launch_z_fe<PZ, W, 6>(sh, im, in, ks, om, on, tw, s);
+  return launch_z_fe<PZ, W, DDS_MAX_FIELDS>(sh, im, in, ks, om, on, tw, s);
 }
 
 template <int M>
@@ -708,7 +739,15 @@ cudaError_t dispatch_x_inv(const Shape &sh, const float2 *im, const float2 *in, 
 
 }  // namespace
 
-int stress_launch_count(const Shape &) { return 5; }
+int stress_launch_count(const Shape &sh, const Collapse &col) {
+  int direct = 0, accum = 0;
+  for (int g = 0; g < col.ngroups; ++g) {
+    if (col.nd[g] == 0) continue;
+    if ((sh.nx % 2 == 0) && col.nf[g] == 1 && col.nd[g] == 1) direct = 1;
+    else accum = 1;
+  }
+  return 4 + direct + accum;   // float32 densities; bfloat16 ones use the accumulating kernel
+}
 
 int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s) {
   const Shape &sh = ctx->shape;

@@ -60,11 +60,17 @@ enum {
   DDS_OPT_NEAR_RADIUS = 1, /* near-field radius in units of the largest cell edge
                               (Sec. 2.3 "several nearest-neighbour shells"); default 3;
                               0 disables subdivision.  Invalidates built kernels. */
-  DDS_OPT_Z_LANES = 2      /* schedule of the fused z pass: 0 = automatic (default);
+  DDS_OPT_Z_LANES = 2,     /* schedule of the fused z pass: 0 = automatic (default);
                               -1 = shared-memory tiles; 1, 2, 4, 8 = register-only kernel
                               with that many lanes per (kx, ky) column (needs padded
                               z size <= 64 and <= 4 combined fields).  Same result up to
                               rounding; a tuning knob.  Invalidates built kernels. */
+  DDS_OPT_SPECTRA_FP16 = 3 /* 1: store the cached kernel spectra as FP16 with one FP32
+                              scale per (component, field) -- half the bytes of the
+                              dominant pass; arithmetic stays FP32.  Error: about 1e-4
+                              relative L2 against the FP64 sum (tested bound 5e-4)
+                              instead of 1e-5.  0 (default): FP32.  Invalidates built
+                              kernels. */
 };
 
 /* Limits of this build. */

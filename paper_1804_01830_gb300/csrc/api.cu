@@ -106,6 +106,8 @@ int next_pow2(int v) {
 
 void free_buffers(dds_ctx *ctx) {
   cudaFree(ctx->kspec);
+  cudaFree(ctx->kscale);
+  ctx->kscale = nullptr;
   cudaFree(ctx->bufA);
   cudaFree(ctx->bufB);
   cudaFree(ctx->nyqA);
@@ -252,12 +254,14 @@ int alloc_buffers(dds_ctx *ctx) {
   if (err == cudaSuccess) err = cudaMalloc(&ctx->bufB, b * sizeof(float2));
   if (err == cudaSuccess) err = cudaMalloc(&ctx->nyqA, na * sizeof(float2));
   if (err == cudaSuccess) err = cudaMalloc(&ctx->nyqB, nb * sizeof(float2));
-  if (err == cudaSuccess) err = cudaMalloc(&ctx->kspec, ks * sizeof(float));
+  const size_t vbytes = ctx->spectra_fp16 ? 2 : sizeof(float);
+  if (err == cudaSuccess) err = cudaMalloc(&ctx->kspec, ks * vbytes);
+  if (err == cudaSuccess && ctx->spectra_fp16) err = cudaMalloc(&ctx->kscale, 6 * fe * sizeof(float));
   if (err != cudaSuccess) {
     cudaGetLastError();
     free_buffers(ctx);
     return fail(ctx, DDS_ERR_OOM, "build_kernels: cannot allocate %.2f GB of device buffers: %s",
-                ((a + b + na + nb) * 8.0 + ks * 4.0) / 1e9, cudaGetErrorString(err));
+                ((a + b + na + nb) * 8.0 + ks * (double)vbytes) / 1e9, cudaGetErrorString(err));
   }
   ctx->bufA_n = a;
   ctx->bufB_n = b;
@@ -360,6 +364,12 @@ int dds_set_option(dds_ctx *ctx, int key, double value) {
       if (!(value == -1 || value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
         return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: z lanes must be -1, 0, 1, 2, 4 or 8");
       ctx->z_lanes = (int)value;
+      invalidate(ctx);
+      return DDS_OK;
+    case DDS_OPT_SPECTRA_FP16:
+      if (!(value == 0 || value == 1))
+        return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: spectra storage must be 0 (FP32) or 1 (FP16)");
+      ctx->spectra_fp16 = value == 1;
       invalidate(ctx);
       return DDS_OK;
     case DDS_OPT_NEAR_RADIUS:

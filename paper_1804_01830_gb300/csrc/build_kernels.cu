@@ -16,6 +16,8 @@
 // is kept, in FP32, laid out per tile of the fused z pass.
 #include <math.h>
 
+#include <cuda_fp16.h>
+
 #include "dds_fft.cuh"
 #include "dds_internal.h"
 
@@ -268,8 +270,28 @@ __global__ void __launch_bounds__(256) k_cols_d(double2 *data, long os, long rs,
 //   register variant (zg = G > 0):  kspec[warp tile][6][fe][lane][E], E = pz / G, warp
 //     tiles of 32/G columns, lane g * (32/G) + w holding kz = k1 + E bitrev_G(g), k1 < E.
 // Main tiles cover (ky, kx < M) row by row; the Nyquist tiles (kx = M) follow.
+__device__ __forceinline__ void store_val(float *p, double v) { *p = (float)v; }
+__device__ __forceinline__ void store_val(__half *p, double v) { *p = __float2half_rn((float)v); }
+
+// Largest |Im| of one spectrum (for the FP16 scale); bit patterns of non-negative
+// doubles order like unsigned integers.
+__global__ void k_absmax_imag(const double2 *spec, long n, unsigned long long *out) {
+  double m = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(spec[i].y));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// FP16 scale of (component c, field e): the largest |value| after the FFT scaling.
+__global__ void k_store_scale(const unsigned long long *amax, double scale, float *kscale, int idx) {
+  const double m = __longlong_as_double((long long)*amax) * scale;
+  kscale[idx] = m > 0.0 ? (float)m : 1.0f;
+}
+
+template <typename OT>
 __global__ void k_extract(const double2 *spec, int M, int py, int pz, int wz, int zg, int fe, int e, int c,
-                          double scale, float *kspec) {
+                          double scale, const unsigned long long *amax, OT *kspec) {
   const int cw = zg > 0 ? 32 / zg : wz;                  // columns per tile
   const int E = zg > 0 ? pz / zg : 0;                     // registers per lane
   const long per_tile = zg > 0 ? 32L * E : (long)pz * wz;
@@ -298,8 +320,12 @@ __global__ void k_extract(const double2 *spec, int M, int py, int pz, int wz, in
     ky = (int)(tau - tiles_main) * cw + w;
     kx = M;
   }
-  const double v = spec[((long)kz * py + ky) * (M + 1) + kx].y;
-  kspec[((tau * 6 + c) * fe + e) * per_tile + r] = (float)(v * scale);
+  double v = spec[((long)kz * py + ky) * (M + 1) + kx].y * scale;
+  if (amax != nullptr) {                 // FP16 storage: values relative to the largest
+    const double m = __longlong_as_double((long long)*amax) * scale;
+    if (m > 0.0) v /= m;
+  }
+  store_val(&kspec[((tau * 6 + c) * fe + e) * per_tile + r], v);
 }
 
 template <int M>
@@ -407,13 +433,16 @@ int build_spectra(dds_ctx *ctx, cudaStream_t s) {
   double *tab = nullptr;
   double2 *spec = nullptr;
   int *d_near = nullptr;
+  unsigned long long *d_amax = nullptr;
   cudaError_t err = cudaMallocAsync(&tab, sizeof(double) * 6 * P, s);
+  if (err == cudaSuccess) err = cudaMallocAsync(&d_amax, sizeof(unsigned long long), s);
   if (err == cudaSuccess) err = cudaMallocAsync(&spec, sizeof(double2) * nspec, s);
   if (err == cudaSuccess && n_near > 0) err = cudaMallocAsync(&d_near, sizeof(int) * 3 * n_near, s);
   if (err != cudaSuccess) {
     cudaFreeAsync(tab, s);
     cudaFreeAsync(spec, s);
     cudaFreeAsync(d_near, s);
+    cudaFreeAsync(d_amax, s);
     cudaGetLastError();
     return fail(ctx, DDS_ERR_OOM, "build_kernels: cannot allocate %.2f GB of FP64 table workspace: %s",
                 (sizeof(double) * 6.0 * P + sizeof(double2) * (double)nspec) / 1e9, cudaGetErrorString(err));
@@ -440,15 +469,27 @@ int build_spectra(dds_ctx *ctx, cudaStream_t s) {
         err = cols_dispatch(pz, spec, 1, 0, (long)py * (M + 1), (long)py * (M + 1), ctx->tw.f64, s);
       if (err == cudaSuccess) {
         const long n = (long)py * (M + 1) * pz;
-        k_extract<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(spec, M, py, pz, sh.wz, sh.zreg_g, sh.fe, e, c,
-                                                              scale, ctx->kspec);
-        err = cudaGetLastError();
+        if (ctx->spectra_fp16) {
+          err = cudaMemsetAsync(d_amax, 0, sizeof(unsigned long long), s);
+          if (err == cudaSuccess) {
+            k_absmax_imag<<<1024, 256, 0, s>>>(spec, nspec, d_amax);
+            k_store_scale<<<1, 1, 0, s>>>(d_amax, scale, ctx->kscale, c * sh.fe + e);
+            k_extract<__half><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+                spec, M, py, pz, sh.wz, sh.zreg_g, sh.fe, e, c, scale, d_amax, static_cast<__half *>(ctx->kspec));
+            err = cudaGetLastError();
+          }
+        } else {
+          k_extract<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+              spec, M, py, pz, sh.wz, sh.zreg_g, sh.fe, e, c, scale, nullptr, static_cast<float *>(ctx->kspec));
+          err = cudaGetLastError();
+        }
       }
     }
   }
   cudaFreeAsync(tab, s);
   cudaFreeAsync(spec, s);
   cudaFreeAsync(d_near, s);
+  cudaFreeAsync(d_amax, s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "build_kernels: %s", cudaGetErrorString(err));
   return DDS_OK;

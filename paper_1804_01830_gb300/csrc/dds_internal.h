@@ -76,8 +76,10 @@ struct dds_ctx {
   bool built = false;
   // device memory
   dds::Twiddles tw;
-  float *kspec = nullptr;               // [tile][6][fe][pz][wz]
-  size_t kspec_floats = 0;
+  void *kspec = nullptr;                // kernel spectra (layout of the z pass), FP32 or FP16
+  float *kscale = nullptr;              // FP16 storage: scale per (component, field); else null
+  size_t kspec_floats = 0;              // number of stored values
+  bool spectra_fp16 = false;            // option: store the kernel spectra as FP16
   float2 *bufA = nullptr, *bufB = nullptr;        // main work buffers
   float2 *nyqA = nullptr, *nyqB = nullptr;        // Nyquist-column buffers
   size_t bufA_n = 0, bufB_n = 0, nyqA_n = 0, nyqB_n = 0;

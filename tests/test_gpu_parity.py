@@ -40,8 +40,15 @@ def rel_l2_per_component(got, ref):
     return np.array(out)
 
 
-def gpu_stress(dds, p, dtype=torch.float32, n_near=None):
-    ctx = dds.context_for(p, n_near=n_near)
+def gpu_stress(dds, p, dtype=torch.float32, n_near=None, fp16_spectra=False):
+    ctx = dds.StressContext(0)
+    g = p.geom
+    ctx.set_geometry(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.mu, g.nu).set_families(p.t, p.b)
+    if n_near is not None:
+        ctx.set_option(dds.DDS_OPT_NEAR_RADIUS, n_near)
+    if fp16_spectra:
+        ctx.set_option(dds.DDS_OPT_SPECTRA_FP16, 1)
+    ctx.build_kernels()
     rho = torch.from_numpy(p.rho.astype(np.float32)).to("cuda", dtype=dtype).contiguous()
     sigma = ctx.stress(rho)
     torch.cuda.synchronize()
@@ -236,3 +243,22 @@ def test_error_codes(dds):
     assert float(ctx.stress(rho).abs().max()) == 0.0
     assert ctx.launches_per_stress == 5
     ctx.close()
+
+
+# ------------------------------------------------------ reduced storage ----
+TOL_FP16_SPECTRA = 5e-4     # stated bound of the FP16 kernel-spectrum storage mode
+
+
+@pytest.mark.parametrize("case", ["gaussian_disk", "polycrystal_small"])
+def test_fp16_spectra_within_stated_bound(dds, case):
+    if case == "gaussian_disk":
+        p = W.gaussian_disk_32()                                       # register z pass
+    else:
+        p = W.gan_polycrystal(W.Geometry(40, 32, 24, 0.2e-6, 0.2e-6, 0.05e-6), 1e-6, seed=7)  # 5 fields
+    got = gpu_stress(dds, p, fp16_spectra=True)
+    ref = oracle.stress_direct(p.geom, p.t, p.b, p.rho).T
+    err = rel_l2_per_component(got, ref).max()
+    print(f"FP16 spectra, {case}: rel-L2 {err:.2e}")
+    assert err <= TOL_FP16_SPECTRA
+    full = gpu_stress(dds, p)
+    assert rel_l2_per_component(full, ref).max() <= TOL_STRESS

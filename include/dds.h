@@ -115,6 +115,15 @@ int dds_build_kernels(dds_ctx *ctx, void *cuda_stream);
  * NOT_READY before dds_build_kernels. */
 int dds_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, void *cuda_stream);
 
+/* nb density sets on one context (same geometry and families), evaluated together:
+ * rho [nb][F][nz][ny][nx], sigma [nb][6][nz][ny][nx], both contiguous.  The result for
+ * each set is that of dds_stress; the cached kernel spectra are read from HBM once per
+ * call and shared by all sets (each column tile processes the sets back to back), so
+ * the per-set cost drops below that of nb separate calls.  The work buffers grow to
+ * hold nb sets on first use (that call synchronises the device and allocates); later
+ * calls with up to that many sets allocate nothing.  1 <= nb <= 4096. */
+int dds_stress_multi(dds_ctx *ctx, int nb, const void *rho, int rho_dtype, float *sigma, void *cuda_stream);
+
 /* As dds_stress for n contexts (each built), inputs rho[i] -> sigma[i], all enqueued
  * on one stream in order. */
 int dds_stress_batched(dds_ctx **ctxs, int n, const void **rho, const int *rho_dtype,

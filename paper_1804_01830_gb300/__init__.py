@@ -32,7 +32,8 @@ DDS_OPT_SPECTRA_FP16 = 3
 
 # Every symbol include/dds.h declares.
 EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option",
-           "dds_build_kernels", "dds_stress", "dds_stress_batched", "dds_stress_noalloc", "dds_stress_host",
+           "dds_build_kernels", "dds_stress", "dds_stress_multi", "dds_stress_batched", "dds_stress_noalloc",
+           "dds_stress_host",
            "dds_table_at", "dds_query", "dds_launches_per_stress", "dds_profile_enable",
            "dds_profile_read", "dds_last_error", "dds_destroy")
 
@@ -67,6 +68,7 @@ def load_library():
         "dds_stress_batched": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), ip,
                                 ctypes.POINTER(vp), vp], ctypes.c_int),
         "dds_stress_noalloc": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "dds_stress_multi": ([vp, ctypes.c_int, vp, ctypes.c_int, vp, vp], ctypes.c_int),
         "dds_stress_host": ([vp, vp, vp, vp], ctypes.c_int),
         "dds_table_at": ([vp, dp, dp, lp, ip, dp], ctypes.c_int),
         "dds_query": ([vp, ip, ip, ip, ip], ctypes.c_int),
@@ -132,6 +134,11 @@ def dds_build_kernels(ctx, stream=None):
 def dds_stress(ctx, rho_ptr: int, rho_dtype: int, sigma_ptr: int, stream=None):
     _check(ctx, load_library().dds_stress(ctx, ctypes.c_void_p(rho_ptr), int(rho_dtype),
                                           ctypes.c_void_p(sigma_ptr), _stream_handle(stream)))
+
+
+def dds_stress_multi(ctx, nb: int, rho_ptr: int, rho_dtype: int, sigma_ptr: int, stream=None):
+    _check(ctx, load_library().dds_stress_multi(ctx, int(nb), ctypes.c_void_p(rho_ptr), int(rho_dtype),
+                                                ctypes.c_void_p(sigma_ptr), _stream_handle(stream)))
 
 
 def dds_stress_batched(ctxs, rho_ptrs, rho_dtypes, sigma_ptrs, stream=None):
@@ -253,6 +260,22 @@ class StressContext:
         if sigma is None:
             sigma = torch.empty((6,) + self.shape, dtype=torch.float32, device=rho.device)
         dds_stress(self.handle, rho.data_ptr(), dt, sigma.data_ptr(), stream)
+        return sigma
+
+    def stress_multi(self, rho, sigma=None, stream=None):
+        """rho: CUDA tensor (nb, F, nz, ny, nx) -> sigma (nb, 6, nz, ny, nx); spectra shared by the sets."""
+        import torch
+        if not rho.is_cuda or not rho.is_contiguous() or rho.dim() != 5:
+            raise ValueError("rho must be a contiguous 5-d CUDA tensor (nb, F, nz, ny, nx)")
+        if tuple(rho.shape[1:]) != (self.n_families,) + self.shape:
+            raise ValueError(f"rho has shape {tuple(rho.shape)}")
+        dt = {torch.float32: DDS_F32, torch.bfloat16: DDS_BF16}.get(rho.dtype)
+        if dt is None:
+            raise ValueError(f"unsupported density dtype {rho.dtype}")
+        nb = int(rho.shape[0])
+        if sigma is None:
+            sigma = torch.empty((nb, 6) + self.shape, dtype=torch.float32, device=rho.device)
+        dds_stress_multi(self.handle, nb, rho.data_ptr(), dt, sigma.data_ptr(), stream)
         return sigma
 
     def stress_host(self, rho_host: np.ndarray, sigma_host: np.ndarray | None = None, stream=None):

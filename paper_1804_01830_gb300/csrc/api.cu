@@ -210,6 +210,7 @@ int make_plan(dds_ctx *ctx) {
   sh.fe = ctx->fe;
   sh.wz = 0;
   sh.zreg_g = 0;
+  sh.nb = 1;
   if (sh.pz <= 64 && sh.fe <= 4 && ctx->z_lanes >= 0) {
     // register-only z pass: E = pz / G registers per lane, E in {8, 16}
     int G = ctx->z_lanes;
@@ -240,14 +241,49 @@ int make_plan(dds_ctx *ctx) {
   return DDS_OK;
 }
 
+// Work buffers of the five passes for `nbatch` density sets (complex elements).
+void work_sizes(const Shape &sh, int nbatch, size_t *a, size_t *b, size_t *na, size_t *nb) {
+  const size_t fe = (size_t)std::max(sh.fe, 1) * nbatch, c6 = 6 * (size_t)nbatch;
+  const size_t M = sh.M, ny = sh.ny, nz = sh.nz, py = sh.py;
+  *a = std::max(fe * nz * ny * M, c6 * nz * py * M);
+  *b = std::max(fe * nz * py * M, c6 * nz * ny * M);
+  *na = std::max(fe * ny * nz, c6 * py * nz);
+  *nb = std::max(fe * py * nz, c6 * ny * nz);
+}
+
+int alloc_work(dds_ctx *ctx, int nbatch) {
+  size_t a, b, na, nb;
+  work_sizes(ctx->shape, nbatch, &a, &b, &na, &nb);
+  cudaFree(ctx->bufA);
+  cudaFree(ctx->bufB);
+  cudaFree(ctx->nyqA);
+  cudaFree(ctx->nyqB);
+  ctx->bufA = ctx->bufB = ctx->nyqA = ctx->nyqB = nullptr;
+  ctx->bufA_n = ctx->bufB_n = ctx->nyqA_n = ctx->nyqB_n = 0;
+  ctx->nb_cap = 0;
+  cudaError_t err = cudaMalloc(&ctx->bufA, a * sizeof(float2));
+  if (err == cudaSuccess) err = cudaMalloc(&ctx->bufB, b * sizeof(float2));
+  if (err == cudaSuccess) err = cudaMalloc(&ctx->nyqA, na * sizeof(float2));
+  if (err == cudaSuccess) err = cudaMalloc(&ctx->nyqB, nb * sizeof(float2));
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, DDS_ERR_OOM, "cannot allocate %.2f GB of work buffers for %d density sets: %s",
+                (a + b + na + nb) * 8.0 / 1e9, nbatch, cudaGetErrorString(err));
+  }
+  ctx->bufA_n = a;
+  ctx->bufB_n = b;
+  ctx->nyqA_n = na;
+  ctx->nyqB_n = nb;
+  ctx->nb_cap = nbatch;
+  return DDS_OK;
+}
+
 int alloc_buffers(dds_ctx *ctx) {
   const Shape &sh = ctx->shape;
   const size_t fe = (size_t)std::max(sh.fe, 1);
-  const size_t M = sh.M, ny = sh.ny, nz = sh.nz, py = sh.py, pz = sh.pz;
-  const size_t a = std::max(fe * nz * ny * M, 6 * nz * py * M);
-  const size_t b = std::max(fe * nz * py * M, 6 * nz * ny * M);
-  const size_t na = std::max(fe * ny * nz, 6 * py * nz);
-  const size_t nb = std::max(fe * py * nz, 6 * ny * nz);
+  const size_t M = sh.M, py = sh.py, pz = sh.pz;
+  size_t a, b, na, nb;
+  work_sizes(sh, 1, &a, &b, &na, &nb);
   const size_t ks = py * (M + 1) * pz * 6 * fe;   // one FP32 value per (k, component, field)
   free_buffers(ctx);
   cudaError_t err = cudaMalloc(&ctx->bufA, a * sizeof(float2));
@@ -267,6 +303,7 @@ int alloc_buffers(dds_ctx *ctx) {
   ctx->bufB_n = b;
   ctx->nyqA_n = na;
   ctx->nyqB_n = nb;
+  ctx->nb_cap = 1;
   ctx->kspec_floats = ks;
   return DDS_OK;
 }
@@ -417,6 +454,32 @@ int dds_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, void 
     return err == cudaSuccess ? DDS_OK : fail(ctx, DDS_ERR_CUDA, "stress: %s", cudaGetErrorString(err));
   }
   return enqueue_stress(ctx, rho, rho_dtype, sigma, s);
+}
+
+int dds_stress_multi(dds_ctx *ctx, int nb, const void *rho, int rho_dtype, float *sigma, void *cuda_stream) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!ctx->built) return fail(ctx, DDS_ERR_NOT_READY, "stress_multi: call dds_build_kernels first");
+  if (nb < 1 || nb > 4096) return fail(ctx, DDS_ERR_INVALID_ARG, "stress_multi: nb = %d outside [1, 4096]", nb);
+  if (!rho || !sigma) return fail(ctx, DDS_ERR_INVALID_ARG, "stress_multi: NULL pointer");
+  if (rho_dtype != DDS_F32 && rho_dtype != DDS_BF16)
+    return fail(ctx, DDS_ERR_INVALID_ARG, "stress_multi: unknown density type %d", rho_dtype);
+  if (((uintptr_t)rho & 15) || ((uintptr_t)sigma & 15))
+    return fail(ctx, DDS_ERR_INVALID_ARG, "stress_multi: rho and sigma must be 16-byte aligned");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (ctx->fe == 0) {
+    const cudaError_t err =
+        cudaMemsetAsync(sigma, 0, sizeof(float) * 6 * (size_t)nb * ctx->nx * ctx->ny * ctx->nz, s);
+    return err == cudaSuccess ? DDS_OK : fail(ctx, DDS_ERR_CUDA, "stress_multi: %s", cudaGetErrorString(err));
+  }
+  if (nb > ctx->nb_cap) {
+    // the current buffers may still be in use by work queued on any stream
+    const cudaError_t err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress_multi: %s", cudaGetErrorString(err));
+    const int rc = alloc_work(ctx, nb);
+    if (rc != DDS_OK) return rc;
+  }
+  return enqueue_stress(ctx, rho, rho_dtype, sigma, s, nb);
 }
 
 int dds_stress_batched(dds_ctx **ctxs, int n, const void **rho, const int *rho_dtype, float **sigma,

@@ -36,6 +36,7 @@ struct Shape {
   int fin, fe;        // input families, effective fields
   int wz;             // columns per tile of the fused z pass (shared-memory variant)
   int zreg_g;         // > 0: register-only z pass, pz = 16 * zreg_g, zreg_g lanes per column
+  int nb;             // density sets evaluated together (batch); fields are [b][e], outputs [b][c]
 };
 
 // FP64 description of a box coefficient (Eq. 9b times the cell volume).
@@ -83,6 +84,7 @@ struct dds_ctx {
   float2 *bufA = nullptr, *bufB = nullptr;        // main work buffers
   float2 *nyqA = nullptr, *nyqB = nullptr;        // Nyquist-column buffers
   size_t bufA_n = 0, bufB_n = 0, nyqA_n = 0, nyqB_n = 0;
+  int nb_cap = 1;                       // density sets the work buffers hold
   void *h2d_rho = nullptr;              // staging for dds_stress_host
   float *h2d_sigma = nullptr;
   size_t h2d_rho_bytes = 0, h2d_sigma_bytes = 0;
@@ -115,7 +117,7 @@ CoefGeom make_coef_geom(const dds_ctx *ctx);
 int build_spectra(dds_ctx *ctx, cudaStream_t s);
 
 // Enqueue one stress evaluation.
-int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s);
+int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s, int nb = 1);
 int stress_launch_count(const Shape &sh, const Collapse &col);
 int enqueue_stress_buffers(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, float2 *bufA, float2 *bufB,
                            float2 *nyqA, float2 *nyqB, cudaStream_t s);

@@ -40,6 +40,9 @@ __global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, GroupList 
   const long N = L * sh.nx;
   const long l0 = (long)blockIdx.x * W;
   const int g = gl.g[blockIdx.y];
+  const int b = blockIdx.z;                       // density set of the batch
+  rho_v = BF16 ? (const void *)((const uint16_t *)rho_v + (long)b * sh.fin * L * sh.nx)
+               : (const void *)((const float *)rho_v + (long)b * sh.fin * L * sh.nx);
   const int nxh = (sh.nx + 1) >> 1;
   const bool even = (sh.nx & 1) == 0;
   const float2 *twM = tw + tw_offset(M);
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, GroupList 
     cp_async_wait_all();
     __syncthreads();
     fft_tile<M, W, LD, NT, false, true, false, PB>(buf, twM, tid);
-    const int e = col.e0[g] + d;
+    const int e = b * sh.fe + col.e0[g] + d;
     for (int p = tid; p < W * M; p += NT) {
       const int w = p / M, k = p - w * M;
       const long line = l0 + w;
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(NT) k_x_inv(Shape sh, const float2 *in_main, c
   float2 *buf = smem;
   float2 *xm = smem + tile_elems<M, LD, PB, W>();
   const int tid = threadIdx.x;
-  const long L = 6L * sh.nz * sh.ny;
+  const long L = 6L * sh.nb * sh.nz * sh.ny;
   const long l0 = (long)blockIdx.x * W;
   for (int p = tid; p < W * M; p += NT) {
     const int w = p / M, k = p - w * M;
@@ -295,7 +298,7 @@ cudaError_t launch_x_fwd_kind(const Shape &sh, const Collapse &col, const GroupL
   constexpr int W = XTile<M>::W, T = XTile<M>::NT;
   const size_t smem = sizeof(float2) * tile_elems<M, W + 1, Plan<M>::r0, W>();
   const long L = (long)sh.ny * sh.nz;
-  dim3 grid((unsigned)((L + W - 1) / W), gl.n);
+  dim3 grid((unsigned)((L + W - 1) / W), gl.n, sh.nb);
   cudaError_t err = prep(k_x_fwd<M, W, T, BF16, DIRECT>, smem);
   if (err != cudaSuccess) return err;
   k_x_fwd<M, W, T, BF16, DIRECT><<<grid, T, smem, s>>>(sh, col, gl, rho, om, on, tw);
@@ -341,7 +344,7 @@ cudaError_t launch_x_inv(const Shape &sh, const float2 *im, const float2 *in, fl
                          cudaStream_t s) {
   constexpr int W = XTile<M>::W, T = XTile<M>::NT;
   const size_t smem = sizeof(float2) * (tile_elems<M, W + 1, Plan<M>::r0, W>() + W);
-  const long L = 6L * sh.nz * sh.ny;
+  const long L = 6L * sh.nb * sh.nz * sh.ny;
   cudaError_t err = prep(k_x_inv<M, W, T>, smem);
   if (err != cudaSuccess) return err;
   k_x_inv<M, W, T><<<(unsigned)((L + W - 1) / W), T, smem, s>>>(sh, im, in, sigma, tw);
@@ -401,8 +404,9 @@ int stress_launch_count(const Shape &sh, const Collapse &col) {
   return 4 + direct + accum;   // float32 densities; bfloat16 ones use the accumulating kernel
 }
 
-int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s) {
-  const Shape &sh = ctx->shape;
+int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s, int nb) {
+  Shape sh = ctx->shape;
+  sh.nb = nb;
   const float2 *tw = ctx->tw.f32;
   cudaEvent_t *ev = nullptr;
   cudaError_t err = cudaSuccess;
@@ -424,12 +428,12 @@ int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, c
   };
   if (err == cudaSuccess) err = dispatch_x_fwd(sh, ctx->col, rho, rho_dtype == DDS_BF16, ctx->bufA, ctx->nyqA, tw, s);
   mark(1);
-  if (err == cudaSuccess) err = dispatch_y<false>(sh, sh.fe, ctx->bufA, ctx->nyqA, ctx->bufB, ctx->nyqB, tw, s);
+  if (err == cudaSuccess) err = dispatch_y<false>(sh, nb * sh.fe, ctx->bufA, ctx->nyqA, ctx->bufB, ctx->nyqB, tw, s);
   mark(2);
   if (err == cudaSuccess)
     err = dispatch_z(sh, ctx->bufB, ctx->nyqB, ctx->kspec, ctx->kscale, ctx->bufA, ctx->nyqA, tw, s);
   mark(3);
-  if (err == cudaSuccess) err = dispatch_y<true>(sh, 6, ctx->bufA, ctx->nyqA, ctx->bufB, ctx->nyqB, tw, s);
+  if (err == cudaSuccess) err = dispatch_y<true>(sh, 6 * nb, ctx->bufA, ctx->nyqA, ctx->bufB, ctx->nyqB, tw, s);
   mark(4);
   if (err == cudaSuccess) err = dispatch_x_inv(sh, ctx->bufB, ctx->nyqB, sigma, tw, s);
   mark(5);

@@ -36,7 +36,14 @@ __global__ void __launch_bounds__(NT) k_zpass(Shape sh, const float2 *in_main, c
   GT *G1 = G0 + (long)fe * TS;
   const long ktiles = M / W;
   const long tiles_main = (long)py * ktiles;
-  const long tau = blockIdx.x;
+  // Consecutive blocks take the same column tile for the density sets of a batch,
+  // so the tile's kernel spectra come from HBM once and from L2 for the others.
+  const long tau = blockIdx.x / sh.nb;
+  const int bset = (int)(blockIdx.x - tau * sh.nb);
+  in_main += bset * ((long)fe * nz * py * M);
+  in_nyq += bset * ((long)fe * py * nz);
+  out_main += bset * (6L * nz * py * M);
+  out_nyq += bset * (6L * py * nz);
   const bool nyq = tau >= tiles_main;
   long ky = 0, kx0 = 0, ky0 = 0;
   if (!nyq) {
@@ -195,11 +202,19 @@ __global__ void __launch_bounds__(128) k_zreg(Shape sh, const float2 *in_main, c
                                               float2 *out_nyq, const float2 *tw) {
   constexpr int P = G * E, CW = 32 / G;
   const int lane = threadIdx.x & 31;
-  const long T = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const long TB = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int M = sh.M, py = sh.py, nz = sh.nz, fe = sh.fe;
   const long wt_main = (long)py * (M / CW);
   const long wt_all = wt_main + py / CW;
+  // Consecutive warps take the same columns for the density sets of a batch, so the
+  // kernel spectra come from HBM once and from L1/L2 for the others.
+  const long T = TB / sh.nb;
+  const int bset = (int)(TB - T * sh.nb);
   if (T >= wt_all) return;                              // whole warp exits together
+  in_main += bset * ((long)fe * nz * py * M);
+  in_nyq += bset * ((long)fe * py * nz);
+  out_main += bset * (6L * nz * py * M);
+  out_nyq += bset * (6L * py * nz);
   const int g = lane / CW, wl = lane - g * CW;
   const bool nyq = T >= wt_main;
   long ky = 0, kx = 0;
@@ -295,7 +310,7 @@ template <int PZ, int W, int FEMAX, typename GT>
 cudaError_t launch_z_fe(const Shape &sh, const float2 *im, const float2 *in, const GT *ks, const float *ksc,
                         float2 *om, float2 *on, const float2 *tw, cudaStream_t s) {
   const size_t smem = (sizeof(float2) * (size_t)(sh.fe + 3) + 2 * sizeof(GT) * (size_t)sh.fe) * PZ * W;
-  const long tiles = (long)sh.py * (sh.M / W) + sh.py / W;
+  const long tiles = ((long)sh.py * (sh.M / W) + sh.py / W) * sh.nb;
   cudaError_t err = prep(k_zpass<PZ, W, FEMAX, GT>, smem);
   if (err != cudaSuccess) return err;
   k_zpass<PZ, W, FEMAX, GT><<<(unsigned)tiles, NT, smem, s>>>(sh, im, in, ks, ksc, om, on, tw);
@@ -334,7 +349,7 @@ template <int E, int G, int FE, typename GT>
 cudaError_t launch_zreg(const Shape &sh, const float2 *im, const float2 *in, const GT *ks, const float *ksc,
                         float2 *om, float2 *on, const float2 *tw, cudaStream_t s) {
   constexpr int CW = 32 / G;
-  const long warps = (long)sh.py * (sh.M / CW) + sh.py / CW;
+  const long warps = ((long)sh.py * (sh.M / CW) + sh.py / CW) * sh.nb;
   k_zreg<E, G, FE, GT><<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(sh, im, in, ks, ksc, om, on, tw);
   return cudaGetLastError();
 }

@@ -262,3 +262,25 @@ def test_fp16_spectra_within_stated_bound(dds, case):
     assert err <= TOL_FP16_SPECTRA
     full = gpu_stress(dds, p)
     assert rel_l2_per_component(full, ref).max() <= TOL_STRESS
+
+
+# ------------------------------------------------------------- batches -----
+@pytest.mark.parametrize("case", ["thin", "tall"])
+def test_multi_matches_single_evaluations(dds, case):
+    if case == "thin":          # register z pass
+        g = W.Geometry(64, 48, 16, 0.5e-6, 0.5e-6, 0.2e-6)
+        t, b = W.gan_families()
+        probs = [W.random_problem(g, t[[0, 9]], b[[0, 9]], seed=40 + i) for i in range(3)]
+    else:                       # shared-memory z pass, 5 fields
+        g = W.Geometry(32, 32, 40, 0.2e-6, 0.2e-6, 0.05e-6)
+        probs = [W.gan_polycrystal(g, 1e-6, seed=50 + i) for i in range(3)]
+    ctx = dds.context_for(probs[0])
+    rhos = torch.stack([torch.from_numpy(np.ascontiguousarray(p.rho, dtype=np.float32)) for p in probs]).cuda()
+    multi = ctx.stress_multi(rhos)
+    singles = [ctx.stress(rhos[i].contiguous()) for i in range(len(probs))]
+    torch.cuda.synchronize()
+    for i in range(len(probs)):
+        assert rel_l2_per_component(multi[i].cpu().numpy(), singles[i].cpu().numpy()).max() <= 1e-6
+    ref = oracle.stress_direct(g, probs[1].t, probs[1].b, probs[1].rho).T
+    assert rel_l2_per_component(multi[1].cpu().numpy(), ref).max() <= TOL_STRESS
+    ctx.close()

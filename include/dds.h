@@ -124,6 +124,15 @@ int dds_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, void 
  * calls with up to that many sets allocate nothing.  1 <= nb <= 4096. */
 int dds_stress_multi(dds_ctx *ctx, int nb, const void *rho, int rho_dtype, float *sigma, void *cuda_stream);
 
+/* Evaluation with the per-height statistics of Eq. 20 fused into its last pass: as
+ * dds_stress_multi (nb >= 1 sets; nb = 1 is one dds_stress), and s_out (device,
+ * float32, [nb][6][nz]) receives s_c(h_k) = sqrt((1/(nx ny)) sum_{i,j}
+ * sigma_c(x_i, y_j, h_k)^2), the in-plane RMS of every component at every height.
+ * The sums are accumulated in FP64 by atomic additions, so their rounding depends
+ * on the order of the additions.  Sizes its work buffers like dds_stress_multi. */
+int dds_stress_stats(dds_ctx *ctx, int nb, const void *rho, int rho_dtype, float *sigma, float *s_out,
+                     void *cuda_stream);
+
 /* As dds_stress for n contexts (each built), inputs rho[i] -> sigma[i], all enqueued
  * on one stream in order. */
 int dds_stress_batched(dds_ctx **ctxs, int n, const void **rho, const int *rho_dtype,

@@ -32,7 +32,8 @@ DDS_OPT_SPECTRA_FP16 = 3
 
 # Every symbol include/dds.h declares.
 EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option",
-           "dds_build_kernels", "dds_stress", "dds_stress_multi", "dds_stress_batched", "dds_stress_noalloc",
+           "dds_build_kernels", "dds_stress", "dds_stress_multi", "dds_stress_stats", "dds_stress_batched",
+           "dds_stress_noalloc",
            "dds_stress_host",
            "dds_table_at", "dds_query", "dds_launches_per_stress", "dds_profile_enable",
            "dds_profile_read", "dds_last_error", "dds_destroy")
@@ -69,6 +70,7 @@ def load_library():
                                 ctypes.POINTER(vp), vp], ctypes.c_int),
         "dds_stress_noalloc": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
         "dds_stress_multi": ([vp, ctypes.c_int, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "dds_stress_stats": ([vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
         "dds_stress_host": ([vp, vp, vp, vp], ctypes.c_int),
         "dds_table_at": ([vp, dp, dp, lp, ip, dp], ctypes.c_int),
         "dds_query": ([vp, ip, ip, ip, ip], ctypes.c_int),
@@ -139,6 +141,12 @@ def dds_stress(ctx, rho_ptr: int, rho_dtype: int, sigma_ptr: int, stream=None):
 def dds_stress_multi(ctx, nb: int, rho_ptr: int, rho_dtype: int, sigma_ptr: int, stream=None):
     _check(ctx, load_library().dds_stress_multi(ctx, int(nb), ctypes.c_void_p(rho_ptr), int(rho_dtype),
                                                 ctypes.c_void_p(sigma_ptr), _stream_handle(stream)))
+
+
+def dds_stress_stats(ctx, nb: int, rho_ptr: int, rho_dtype: int, sigma_ptr: int, s_ptr: int, stream=None):
+    _check(ctx, load_library().dds_stress_stats(ctx, int(nb), ctypes.c_void_p(rho_ptr), int(rho_dtype),
+                                                ctypes.c_void_p(sigma_ptr), ctypes.c_void_p(s_ptr),
+                                                _stream_handle(stream)))
 
 
 def dds_stress_batched(ctxs, rho_ptrs, rho_dtypes, sigma_ptrs, stream=None):
@@ -277,6 +285,26 @@ class StressContext:
             sigma = torch.empty((nb, 6) + self.shape, dtype=torch.float32, device=rho.device)
         dds_stress_multi(self.handle, nb, rho.data_ptr(), dt, sigma.data_ptr(), stream)
         return sigma
+
+    def stress_stats(self, rho, sigma=None, stream=None):
+        """sigma and the Eq. 20 in-plane RMS per component and height: returns (sigma, s)
+        with s of shape (6, nz) (or (nb, 6, nz) for a 5-d batch of densities)."""
+        import torch
+        batched = rho.dim() == 5
+        r = rho if batched else rho.unsqueeze(0)
+        if not r.is_cuda or not r.is_contiguous():
+            raise ValueError("rho must be a contiguous CUDA tensor")
+        if tuple(r.shape[1:]) != (self.n_families,) + self.shape:
+            raise ValueError(f"rho has shape {tuple(rho.shape)}")
+        dt = {torch.float32: DDS_F32, torch.bfloat16: DDS_BF16}.get(r.dtype)
+        if dt is None:
+            raise ValueError(f"unsupported density dtype {r.dtype}")
+        nb = int(r.shape[0])
+        if sigma is None:
+            sigma = torch.empty((nb, 6) + self.shape, dtype=torch.float32, device=r.device)
+        s = torch.empty((nb, 6, self.shape[0]), dtype=torch.float32, device=r.device)
+        dds_stress_stats(self.handle, nb, r.data_ptr(), dt, sigma.data_ptr(), s.data_ptr(), stream)
+        return (sigma, s) if batched else (sigma[0], s[0])
 
     def stress_host(self, rho_host: np.ndarray, sigma_host: np.ndarray | None = None, stream=None):
         rho_host = np.ascontiguousarray(rho_host, dtype=np.float32)

@@ -482,6 +482,45 @@ int dds_stress_multi(dds_ctx *ctx, int nb, const void *rho, int rho_dtype, float
   return enqueue_stress(ctx, rho, rho_dtype, sigma, s, nb);
 }
 
+int dds_stress_stats(dds_ctx *ctx, int nb, const void *rho, int rho_dtype, float *sigma, float *s_out,
+                     void *cuda_stream) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!ctx->built) return fail(ctx, DDS_ERR_NOT_READY, "stress_stats: call dds_build_kernels first");
+  if (nb < 1 || nb > 4096) return fail(ctx, DDS_ERR_INVALID_ARG, "stress_stats: nb = %d outside [1, 4096]", nb);
+  if (!rho || !sigma || !s_out) return fail(ctx, DDS_ERR_INVALID_ARG, "stress_stats: NULL pointer");
+  if (rho_dtype != DDS_F32 && rho_dtype != DDS_BF16)
+    return fail(ctx, DDS_ERR_INVALID_ARG, "stress_stats: unknown density type %d", rho_dtype);
+  if (((uintptr_t)rho & 15) || ((uintptr_t)sigma & 15))
+    return fail(ctx, DDS_ERR_INVALID_ARG, "stress_stats: rho and sigma must be 16-byte aligned");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t ns = 6 * (size_t)nb * ctx->nz;
+  if (ctx->fe == 0) {
+    cudaError_t err = cudaMemsetAsync(sigma, 0, sizeof(float) * 6 * (size_t)nb * ctx->nx * ctx->ny * ctx->nz, s);
+    if (err == cudaSuccess) err = cudaMemsetAsync(s_out, 0, sizeof(float) * ns, s);
+    return err == cudaSuccess ? DDS_OK : fail(ctx, DDS_ERR_CUDA, "stress_stats: %s", cudaGetErrorString(err));
+  }
+  if (nb > ctx->nb_cap || (int)ns > ctx->stats_cap) {
+    const cudaError_t err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress_stats: %s", cudaGetErrorString(err));
+    if (nb > ctx->nb_cap) {
+      const int rc = alloc_work(ctx, nb);
+      if (rc != DDS_OK) return rc;
+    }
+    if ((int)ns > ctx->stats_cap) {
+      cudaFree(ctx->stats);
+      ctx->stats = nullptr;
+      ctx->stats_cap = 0;
+      if (cudaMalloc(&ctx->stats, sizeof(double) * ns) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, DDS_ERR_OOM, "stress_stats: cannot allocate %zu bytes", sizeof(double) * ns);
+      }
+      ctx->stats_cap = (int)ns;
+    }
+  }
+  return enqueue_stress(ctx, rho, rho_dtype, sigma, s, nb, ctx->stats, s_out);
+}
+
 int dds_stress_batched(dds_ctx **ctxs, int n, const void **rho, const int *rho_dtype, float **sigma,
                        void *cuda_stream) {
   if (!ctxs || n < 0 || (n > 0 && (!rho || !sigma))) return DDS_ERR_INVALID_ARG;
@@ -620,6 +659,7 @@ void dds_destroy(dds_ctx *ctx) {
     free_twiddles(&ctx->tw);
     cudaFree(ctx->h2d_rho);
     cudaFree(ctx->h2d_sigma);
+    cudaFree(ctx->stats);
     for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
   }
   delete ctx;

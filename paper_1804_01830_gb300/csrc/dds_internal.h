@@ -85,6 +85,8 @@ struct dds_ctx {
   float2 *nyqA = nullptr, *nyqB = nullptr;        // Nyquist-column buffers
   size_t bufA_n = 0, bufB_n = 0, nyqA_n = 0, nyqB_n = 0;
   int nb_cap = 1;                       // density sets the work buffers hold
+  double *stats = nullptr;              // Eq. 20 sums, [set][6][nz]
+  int stats_cap = 0;
   void *h2d_rho = nullptr;              // staging for dds_stress_host
   float *h2d_sigma = nullptr;
   size_t h2d_rho_bytes = 0, h2d_sigma_bytes = 0;
@@ -117,7 +119,8 @@ CoefGeom make_coef_geom(const dds_ctx *ctx);
 int build_spectra(dds_ctx *ctx, cudaStream_t s);
 
 // Enqueue one stress evaluation.
-int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s, int nb = 1);
+int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s, int nb = 1,
+                   double *stats = nullptr, float *s_out = nullptr);
 int stress_launch_count(const Shape &sh, const Collapse &col);
 int enqueue_stress_buffers(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, float2 *bufA, float2 *bufB,
                            float2 *nyqA, float2 *nyqB, cudaStream_t s);

@@ -222,9 +222,11 @@ __global__ void __launch_bounds__(NT) k_ypass(Shape sh, int nf, const float2 *in
 
 
 // ---------------------------------------------------------------- x inverse --
+// stats != nullptr: also accumulate sum_x sigma^2 of every line into
+// stats[(set * 6 + c) * nz + z] (the per-height sums of Eq. 20).
 template <int M, int W, int NT>
 __global__ void __launch_bounds__(NT) k_x_inv(Shape sh, const float2 *in_main, const float2 *in_nyq,
-                                              float *sigma, const float2 *tw) {
+                                              float *sigma, const float2 *tw, double *stats) {
   constexpr int LD = W + 1, PB = Plan<M>::r0;
   extern __shared__ float2 smem[];
   float2 *buf = smem;
@@ -275,6 +277,9 @@ __global__ void __launch_bounds__(NT) k_x_inv(Shape sh, const float2 *in_main, c
   fft_tile<M, W, LD, NT, true, false, true, PB>(buf, tw + tw_offset(M), tid);
   const int nxh = (sh.nx + 1) >> 1;
   const bool even = (sh.nx & 1) == 0;
+  float *lsum = reinterpret_cast<float *>(xm + W);     // per-line sums of squares (stats only)
+  if (stats != nullptr && tid < W) lsum[tid] = 0.f;
+  if (stats != nullptr) __syncthreads();
   for (int p = tid; p < W * nxh; p += NT) {
     const int w = p / nxh, n = p - w * nxh;
     const long line = l0 + w;
@@ -287,7 +292,21 @@ __global__ void __launch_bounds__(NT) k_x_inv(Shape sh, const float2 *in_main, c
       dst[0] = v.x;
       if (2 * n + 1 < sh.nx) dst[1] = v.y;
     }
+    if (stats != nullptr) atomicAdd(&lsum[w], v.x * v.x + ((2 * n + 1 < sh.nx) ? v.y * v.y : 0.f));
   }
+  if (stats != nullptr) {
+    __syncthreads();
+    if (tid < W && l0 + tid < L) {
+      const long line = l0 + tid;
+      atomicAdd(&stats[line / sh.ny], (double)lsum[tid]);   // line / ny = (set * 6 + c) * nz + z
+    }
+  }
+}
+
+// s = sqrt(sum / (nx ny)) for every (set, component, height).
+__global__ void k_stats_finish(const double *sums, long n, double inv_plane, float *s_out) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) s_out[i] = (float)sqrt(sums[i] * inv_plane);
 }
 
 // ------------------------------------------------------------ dispatch ------
@@ -341,13 +360,13 @@ cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in
 
 template <int M>
 cudaError_t launch_x_inv(const Shape &sh, const float2 *im, const float2 *in, float *sigma, const float2 *tw,
-                         cudaStream_t s) {
+                         cudaStream_t s, double *stats) {
   constexpr int W = XTile<M>::W, T = XTile<M>::NT;
-  const size_t smem = sizeof(float2) * (tile_elems<M, W + 1, Plan<M>::r0, W>() + W);
+  const size_t smem = sizeof(float2) * (tile_elems<M, W + 1, Plan<M>::r0, W>() + W) + sizeof(float) * W;
   const long L = 6L * sh.nb * sh.nz * sh.ny;
   cudaError_t err = prep(k_x_inv<M, W, T>, smem);
   if (err != cudaSuccess) return err;
-  k_x_inv<M, W, T><<<(unsigned)((L + W - 1) / W), T, smem, s>>>(sh, im, in, sigma, tw);
+  k_x_inv<M, W, T><<<(unsigned)((L + W - 1) / W), T, smem, s>>>(sh, im, in, sigma, tw, stats);
   return cudaGetLastError();
 }
 
@@ -380,14 +399,14 @@ cudaError_t dispatch_y(const Shape &sh, int nf, const float2 *im, const float2 *
 
 
 cudaError_t dispatch_x_inv(const Shape &sh, const float2 *im, const float2 *in, float *sigma, const float2 *tw,
-                           cudaStream_t s) {
+                           cudaStream_t s, double *stats = nullptr) {
   switch (sh.M) {
-    case 16: return launch_x_inv<16>(sh, im, in, sigma, tw, s);
-    case 32: return launch_x_inv<32>(sh, im, in, sigma, tw, s);
-    case 64: return launch_x_inv<64>(sh, im, in, sigma, tw, s);
-    case 128: return launch_x_inv<128>(sh, im, in, sigma, tw, s);
-    case 256: return launch_x_inv<256>(sh, im, in, sigma, tw, s);
-    case 512: return launch_x_inv<512>(sh, im, in, sigma, tw, s);
+    case 16: return launch_x_inv<16>(sh, im, in, sigma, tw, s, stats);
+    case 32: return launch_x_inv<32>(sh, im, in, sigma, tw, s, stats);
+    case 64: return launch_x_inv<64>(sh, im, in, sigma, tw, s, stats);
+    case 128: return launch_x_inv<128>(sh, im, in, sigma, tw, s, stats);
+    case 256: return launch_x_inv<256>(sh, im, in, sigma, tw, s, stats);
+    case 512: return launch_x_inv<512>(sh, im, in, sigma, tw, s, stats);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -404,7 +423,8 @@ int stress_launch_count(const Shape &sh, const Collapse &col) {
   return 4 + direct + accum;   // float32 densities; bfloat16 ones use the accumulating kernel
 }
 
-int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s, int nb) {
+int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s, int nb,
+                   double *stats, float *s_out) {
   Shape sh = ctx->shape;
   sh.nb = nb;
   const float2 *tw = ctx->tw.f32;
@@ -435,7 +455,13 @@ int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, c
   mark(3);
   if (err == cudaSuccess) err = dispatch_y<true>(sh, 6 * nb, ctx->bufA, ctx->nyqA, ctx->bufB, ctx->nyqB, tw, s);
   mark(4);
-  if (err == cudaSuccess) err = dispatch_x_inv(sh, ctx->bufB, ctx->nyqB, sigma, tw, s);
+  if (err == cudaSuccess && stats != nullptr) err = cudaMemsetAsync(stats, 0, sizeof(double) * 6 * nb * sh.nz, s);
+  if (err == cudaSuccess) err = dispatch_x_inv(sh, ctx->bufB, ctx->nyqB, sigma, tw, s, stats);
+  if (err == cudaSuccess && stats != nullptr) {
+    const long n = 6L * nb * sh.nz;
+    k_stats_finish<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(stats, n, 1.0 / ((double)sh.nx * sh.ny), s_out);
+    err = cudaGetLastError();
+  }
   mark(5);
   if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress: kernel launch failed: %s", cudaGetErrorString(err));
   return DDS_OK;

@@ -284,3 +284,34 @@ def test_multi_matches_single_evaluations(dds, case):
     ref = oracle.stress_direct(g, probs[1].t, probs[1].b, probs[1].rho).T
     assert rel_l2_per_component(multi[1].cpu().numpy(), ref).max() <= TOL_STRESS
     ctx.close()
+
+
+# ---------------------------------------------------- Eq. 20 statistics ----
+def plane_rms(sig):
+    """Eq. 20: s_c(h_k) = sqrt(mean over the (x, y) plane of sigma_c^2), shape (6, nz)."""
+    sig = np.asarray(sig, np.float64)
+    return np.sqrt((sig ** 2).mean(axis=(-1, -2)))
+
+
+def test_eq20_statistics_fused_into_the_evaluation(dds):
+    p = W.gan_polycrystal(W.Geometry(40, 32, 24, 0.2e-6, 0.2e-6, 0.05e-6), 1e-6, seed=8)
+    ctx = dds.context_for(p)
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho, dtype=np.float32)).cuda()
+    sig, s = ctx.stress_stats(rho)
+    torch.cuda.synchronize()
+    sig = sig.cpu().numpy()
+    s = s.cpu().numpy()
+    assert s.shape == (6, p.geom.nz)
+    assert np.abs(s - plane_rms(sig)).max() <= 1e-6 * np.abs(s).max()
+    ref = oracle.stress_direct(p.geom, p.t, p.b, p.rho).T.reshape(6, p.geom.nz, p.geom.ny, p.geom.nx)
+    s_ref = plane_rms(ref)
+    for c in range(6):
+        assert np.linalg.norm(s[c] - s_ref[c]) <= TOL_STRESS * np.linalg.norm(s_ref[c])
+    # same statistics for a batch of two sets
+    rho2 = torch.stack([rho, 0.5 * rho]).contiguous()
+    sig2, s2 = ctx.stress_stats(rho2)
+    torch.cuda.synchronize()
+    s2 = s2.cpu().numpy()
+    assert np.abs(s2[0] - s).max() <= 1e-6 * np.abs(s).max()
+    assert np.abs(s2[1] - 0.5 * s).max() <= 1e-5 * np.abs(s).max()
+    ctx.close()

@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-comparator", action="store_true", help="skip the cuFFT comparator")
     ap.add_argument("--no-reduced", action="store_true", help="skip the FP16-spectra measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency measurement")
+    ap.add_argument("--serving-seconds", type=float, default=5.0)
     return ap.parse_args()
 
 
@@ -231,6 +233,71 @@ def cufft_comparator(p, q, steps: int = 20, warmup: int = 3):
     return res
 
 
+# ----------------------------------------------------------------- serving --
+def serving_benchmark(device: int, duration: float, rate: float = 200.0, budget: float = 150e9, seed: int = 0):
+    """Poisson stream of stress requests (mixed grids, cell aspects and family sets)
+    through the continuous-batching server; kernel spectra cached per geometry (warmed
+    before the timed stream), admission by an HBM budget.  Latency = submission to the
+    stress array on the host."""
+    import torch
+
+    from paper_1804_01830_gb300.serve import StressRequest, StressServer
+    arrivals = W.serving_stream(seed, duration, rate)
+    kinds = sorted({(gi, ai, fi) for _, gi, ai, fi in arrivals})
+    dens = {}
+    cases = {}
+    for gi, ai, fi in kinds:
+        c = W.serving_problem(gi, ai, fi, seed=seed)
+        if (gi, fi) not in dens:
+            dens[(gi, fi)] = torch.from_numpy(c.rho).pin_memory()
+        cases[(gi, ai, fi)] = c
+
+    def request(kind):
+        c = cases[kind]
+        g = c.geom
+        return StressRequest((g.nx, g.ny, g.nz), (g.dx, g.dy, g.dz), g.mu, g.nu, c.t, c.b, dens[(kind[0], kind[2])])
+
+    srv = StressServer(device=device, hbm_budget=budget, n_streams=4, max_batch=2)
+    t0 = time.perf_counter()
+    for kind in kinds:
+        srv.warm(request(kind))
+    build_s = time.perf_counter() - t0
+    for kind in kinds:                     # untimed: one request per kind primes pinned buffers
+        srv.submit(request(kind)).result(timeout=600)
+    srv.latencies.clear()
+
+    done = threading.Semaphore(0)
+    errors = []
+
+    def finished(f):                       # results are consumed and dropped as they arrive
+        if f.exception() is not None:
+            errors.append(f.exception())
+        done.release()
+
+    cells = 0
+    t0 = time.perf_counter()
+    for ta, gi, ai, fi in arrivals:
+        dt = ta - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        srv.submit(request((gi, ai, fi))).add_done_callback(finished)
+        cells += cases[(gi, ai, fi)].geom.n_cells
+    for _ in arrivals:
+        if not done.acquire(timeout=600):
+            raise RuntimeError("serving benchmark timed out")
+    wall = time.perf_counter() - t0
+    lat = srv.latency_ms()
+    srv.close()
+    if errors:
+        raise errors[0]
+    return {"arrivals": f"Poisson {rate:g}/s for {duration:g} s", "requests": len(arrivals),
+            "grids": [list(gr) for gr in W.SERVING_GRIDS], "dz_over_dx": W.SERVING_ASPECTS,
+            "family_sets": W.SERVING_FAMILY_SETS, "contexts": len(kinds), "kernel_build_s": build_s,
+            "p50_ms": lat.get("p50"), "p99_ms": lat.get("p99"), "mean_ms": lat.get("mean"),
+            "max_ms": lat.get("max"), "throughput_req_per_s": len(arrivals) / wall,
+            "cells_per_s": cells / wall, "hbm_budget_gb": budget / 1e9}
+
+
 # ----------------------------------------------------------- CPU baseline --
 def oracle_sample(p, seconds: float, seed: int = 0):
     """Time the FP64 oracle's direct sum on a bounded sample of target cells."""
@@ -395,6 +462,10 @@ def run_ours(args):
                    "stated_bound_vs_fp64": 5e-4}
         ctx16.close()
 
+    serving = None
+    if not args.no_serving and rank == 0 and world == 1:
+        serving = serving_benchmark(local, args.serving_seconds)
+
     comparator = None
     if not args.no_comparator:
         comparator = cufft_comparator(p, q)
@@ -426,6 +497,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_comparator": comparator,
         "reduced_storage": reduced,
+        "serving": serving,
         "cpu_baseline": cpu,
         "gpu_launches": K * ctx.launches_per_stress,
         "clocks": clk,

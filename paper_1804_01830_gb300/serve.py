@@ -1,0 +1,258 @@
+"""Continuous-batching stress server on one GPU.
+
+Requests (grid geometry, dislocation families, densities) arrive at any time from
+any thread.  A scheduler thread
+
+  * keeps one built context per (geometry, families) in a cache, so the kernel
+    spectra of a geometry stay resident in HBM and are built once (Sec. 2.3: the
+    coefficients are computed once per geometry); idle contexts are evicted, least
+    recently used first, when the HBM budget needs room;
+  * admits a request when its device footprint (the context, if not yet resident,
+    plus the request's density and stress buffers) fits the budget;
+  * evaluates the waiting requests of one context together (one dds_stress_multi
+    call, the spectra read once), and runs different contexts on different CUDA
+    streams, so work admitted while other work is on the GPU overlaps with it;
+  * returns results through futures and records each request's latency
+    (submission to result on the host).
+
+A context has one set of work buffers, so at most one evaluation per context is in
+flight; requests for a busy context wait while other contexts proceed.
+"""
+from __future__ import annotations
+
+import queue
+import threading
+import time
+from collections import OrderedDict
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import DDS_F32, StressContext
+
+
+@dataclass(eq=False)
+class StressRequest:
+    grid: tuple            # (nx, ny, nz)
+    cells: tuple           # (dx, dy, dz) in m
+    mu: float
+    nu: float
+    t: np.ndarray          # (F, 3)
+    b: np.ndarray          # (F, 3)
+    rho: object            # (F, nz, ny, nx) float32: torch tensor (pinned host or device) or numpy
+    submitted: float = field(default=0.0)
+
+    def key(self):
+        return (tuple(int(v) for v in self.grid), tuple(float(v) for v in self.cells), float(self.mu),
+                float(self.nu), np.asarray(self.t, np.float64).tobytes(), np.asarray(self.b, np.float64).tobytes())
+
+
+class _Entry:
+    def __init__(self, ctx: StressContext, nbytes: int):
+        self.ctx = ctx
+        self.nbytes = nbytes
+        self.busy = False
+
+
+def context_bytes(q: dict, grid, n_families: int, nb: int = 1) -> int:
+    """Device bytes of a built context: FP32 kernel spectra plus work buffers for nb sets."""
+    nx, ny, nz = grid
+    fe, px, py, pz = q["n_fields"], q["px"], q["py"], q["pz"]
+    m = px // 2
+    spectra = 6 * max(fe, 1) * py * (m + 1) * pz * 4
+    a = max(fe * nz * ny * m, 6 * nz * py * m) * nb
+    b = max(fe * nz * py * m, 6 * nz * ny * m) * nb
+    return spectra + (a + b) * 8 + (2 << 20)
+
+
+class StressServer:
+    def __init__(self, device: int = 0, hbm_budget: float = 150e9, n_streams: int = 4, max_batch: int = 8):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.budget = float(hbm_budget)
+        self.max_batch = max_batch
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
+        self.free_streams = list(self.streams)
+        self.cache: "OrderedDict[tuple, _Entry]" = OrderedDict()
+        self.resident = 0
+        self.pending: list = []            # (request, future)
+        self.inflight: list = []           # dicts: event, stream, entry, items, sigma
+        self.inbox: "queue.Queue" = queue.Queue()
+        self.latencies: list = []
+        self.stop_flag = False
+        self.error = None
+        self.thread = threading.Thread(target=self._run, name="stress-scheduler", daemon=True)
+        self.thread.start()
+
+    # ---------------------------------------------------------------- public --
+    def submit(self, req: StressRequest) -> Future:
+        """Queue a request; the future yields sigma (6, nz, ny, nx) as a numpy array."""
+        fut: Future = Future()
+        if isinstance(req.rho, np.ndarray):
+            req.rho = self.torch.from_numpy(np.ascontiguousarray(req.rho, dtype=np.float32)).pin_memory()
+        req.submitted = time.perf_counter()
+        self.inbox.put((req, fut))
+        return fut
+
+    def close(self):
+        self.stop_flag = True
+        self.thread.join()
+        for e in self.cache.values():
+            e.ctx.close()
+        self.cache.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def warm(self, req: StressRequest):
+        """Build (and cache) the context of a request ahead of time (synchronous)."""
+        done = threading.Event()
+        self.inbox.put(("warm", req, done))
+        done.wait()
+
+    # ------------------------------------------------------------- scheduler --
+    def _get_entry(self, req: StressRequest):
+        k = req.key()
+        e = self.cache.get(k)
+        if e is not None:
+            self.cache.move_to_end(k)
+            return e
+        return None
+
+    def _build_entry(self, req: StressRequest):
+        ctx = StressContext(self.device)
+        nx, ny, nz = req.grid
+        dx, dy, dz = req.cells
+        ctx.set_geometry(nx, ny, nz, dx, dy, dz, req.mu, req.nu).set_families(req.t, req.b)
+        ctx.build_kernels(self.streams[0])
+        if self.max_batch > 1:
+            # size the work buffers for a full batch now (growing them later synchronises the device)
+            torch = self.torch
+            with torch.cuda.stream(self.streams[0]):
+                z = torch.zeros((self.max_batch, len(req.t), nz, ny, nx), device=f"cuda:{self.device}")
+                ctx.stress_multi(z, stream=self.streams[0])
+            self.streams[0].synchronize()
+            del z
+        e = _Entry(ctx, context_bytes(ctx.query(), req.grid, len(req.t), self.max_batch))
+        self.cache[req.key()] = e
+        self.resident += e.nbytes
+        return e
+
+    def _make_room(self, need: float) -> bool:
+        while self.resident + need > self.budget:
+            victim = next((k for k, e in self.cache.items() if not e.busy), None)
+            if victim is None:
+                return False
+            e = self.cache.pop(victim)
+            self.resident -= e.nbytes
+            e.ctx.close()
+        return True
+
+    def _io_bytes(self, reqs):
+        return sum(4 * r.rho.numel() * (1 + 6 / max(len(r.t), 1)) for r in reqs)
+
+    def _launch(self, entry: _Entry, items):
+        torch = self.torch
+        stream = self.free_streams.pop()
+        reqs = [r for r, _ in items]
+        with torch.cuda.stream(stream):
+            rho = torch.empty((len(reqs),) + tuple(reqs[0].rho.shape), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+            for i, r in enumerate(reqs):
+                rho[i].copy_(r.rho, non_blocking=True)
+            sigma = entry.ctx.stress_multi(rho, stream=stream)
+            out = torch.empty(sigma.shape, dtype=sigma.dtype, pin_memory=True)
+            out.copy_(sigma, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        entry.busy = True
+        self.inflight.append({"event": ev, "stream": stream, "entry": entry, "items": items,
+                              "keep": (rho, sigma), "out": out, "io": self._io_bytes(reqs)})
+        self.resident += self._io_bytes(reqs)
+
+    def _complete(self):
+        still = []
+        for job in self.inflight:
+            if job["event"].query():
+                out = job["out"].numpy()
+                now = time.perf_counter()
+                for i, (r, fut) in enumerate(job["items"]):
+                    self.latencies.append(now - r.submitted)
+                    fut.set_result(out[i])      # a view of the job's pinned buffer
+                job["entry"].busy = False
+                self.free_streams.append(job["stream"])
+                self.resident -= job["io"]
+            else:
+                still.append(job)
+        self.inflight = still
+
+    def _schedule(self):
+        progressed = True
+        while progressed and self.pending and self.free_streams:
+            progressed = False
+            for idx, (req, fut) in enumerate(self.pending):
+                entry = self._get_entry(req)
+                if entry is not None and entry.busy:
+                    continue                       # its context is on the GPU; try others
+                k = req.key()
+                group = [(r, f) for r, f in self.pending if r.key() == k][: self.max_batch]
+                need = self._io_bytes([r for r, _ in group]) + (0 if entry else 0)
+                if entry is None:
+                    # footprint of a new context is known after planning; build then account
+                    if not self._make_room(need):
+                        continue
+                    entry = self._build_entry(req)
+                    if self.resident + need > self.budget and not self._make_room(need):
+                        continue
+                elif not self._make_room(need):
+                    continue
+                taken = {id(item[1]) for item in group}
+                self.pending = [x for x in self.pending if id(x[1]) not in taken]
+                self._launch(entry, group)
+                progressed = True
+                break
+
+    def _run(self):
+        try:
+            while True:
+                while True:
+                    try:
+                        msg = self.inbox.get_nowait()
+                    except queue.Empty:
+                        break
+                    if msg[0] == "warm":
+                        _, req, done = msg
+                        if self._get_entry(req) is None:
+                            self._make_room(0)
+                            self._build_entry(req)
+                        done.set()
+                    else:
+                        self.pending.append(msg)
+                self._complete()
+                self._schedule()
+                if self.stop_flag and not self.pending and not self.inflight and self.inbox.empty():
+                    return
+                time.sleep(0.0002 if (self.inflight or self.pending) else 0.001)
+        except BaseException as ex:          # surface scheduler failures to every waiter
+            self.error = ex
+            for _, fut in self.pending:
+                if not fut.done():
+                    fut.set_exception(ex)
+            for job in self.inflight:
+                for _, fut in job["items"]:
+                    if not fut.done():
+                        fut.set_exception(ex)
+            raise
+
+    # ------------------------------------------------------------- metrics --
+    def latency_ms(self):
+        lat = np.array(self.latencies) * 1e3
+        if lat.size == 0:
+            return {"n": 0}
+        return {"n": int(lat.size), "p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                "mean": float(lat.mean()), "max": float(lat.max())}

@@ -190,13 +190,22 @@ def voronoi_columns(geom: Geometry, n_seeds: int, seed: int) -> np.ndarray:
     X, Y = cell_centres_xy(geom)
     xs = X.ravel()
     ys = Y.ravel()
+    try:                                     # k-d tree when scipy is present (same nearest seed)
+        from scipy.spatial import cKDTree
+        _, idx = cKDTree(np.stack([sx, sy], axis=1)).query(np.stack([xs, ys], axis=1))
+        return np.asarray(idx, dtype=np.int64).reshape(geom.ny, geom.nx)
+    except ImportError:
+        pass
     best = np.zeros(xs.size, dtype=np.int64)
     bestd = np.full(xs.size, np.inf)
-    for k in range(n_seeds):            # ascending id: strict < keeps the lower id on ties
-        d = (xs - sx[k]) ** 2 + (ys - sy[k]) ** 2
-        m = d < bestd
-        best[m] = k
-        bestd[m] = d[m]
+    chunk = 64
+    for k0 in range(0, n_seeds, chunk):     # ascending ids; argmin keeps the lowest id on ties
+        d = (xs[:, None] - sx[None, k0:k0 + chunk]) ** 2 + (ys[:, None] - sy[None, k0:k0 + chunk]) ** 2
+        j = np.argmin(d, axis=1)
+        dj = d[np.arange(xs.size), j]
+        m = dj < bestd
+        best[m] = k0 + j[m]
+        bestd[m] = dj[m]
     return best.reshape(geom.ny, geom.nx)
 
 
@@ -250,6 +259,56 @@ def sweep_realisation(r: int) -> Problem:
     D = math.exp(math.log(0.5) + (math.log(8.0) - math.log(0.5)) * u[1]) * UM
     g = Geometry(nx, ny, nz, 0.2 * UM, 0.2 * UM, 0.05 * UM)
     return gan_polycrystal(g, D, r, name=f"sweep_{r}")
+
+
+# Serving stream: grids, cell aspects dz/dx (dx = dy = 0.2 um) and family sets drawn
+# per request; one Voronoi polycrystal (2 um grains) per (grid, family set) serves
+# as the density of every request of that kind.
+SERVING_GRIDS = [(64, 64, 64), (128, 128, 64), (256, 256, 128), (512, 512, 64)]
+SERVING_ASPECTS = [0.1, 0.25, 1.0]
+SERVING_FAMILY_SETS = [[0], [1, 4, 8, 15]]        # indices into gan_families(): 1 and 4 families
+
+
+def serving_stream(seed: int, duration: float, rate: float):
+    """Poisson arrivals at `rate` per second for `duration` seconds: list of
+    (arrival time s, grid index, aspect index, family-set index)."""
+    out = []
+    t = 0.0
+    i = 0
+    while True:
+        u = uniform01(seed, np.arange(4 * i, 4 * i + 4))
+        t += -math.log(1.0 - u[0]) / rate
+        if t >= duration:
+            return out
+        out.append((t, min(int(4 * u[1]), 3), min(int(3 * u[2]), 2), min(int(len(SERVING_FAMILY_SETS) * u[3]),
+                                                                           len(SERVING_FAMILY_SETS) - 1)))
+        i += 1
+
+
+@dataclass
+class ServingCase:
+    geom: Geometry
+    t: np.ndarray
+    b: np.ndarray
+    rho: np.ndarray          # (F, nz, ny, nx) float32
+
+
+def serving_problem(grid_idx: int, aspect_idx: int, famset_idx: int, seed: int = 0) -> ServingCase:
+    """Density of one request kind: Voronoi columns (2 um grains) whose grains take the
+    families of the set in turn, each carrying the polycrystal height profile."""
+    nx, ny, nz = SERVING_GRIDS[grid_idx]
+    dx = 0.2 * UM
+    g = Geometry(nx, ny, nz, dx, dx, dx * SERVING_ASPECTS[aspect_idx])
+    n_seeds = max(1, int(round(g.nx * g.dx * g.ny * g.dy / (math.pi * UM ** 2))))
+    grains = voronoi_columns(g, n_seeds, seed)
+    t18, b18 = gan_families()
+    fams = SERVING_FAMILY_SETS[famset_idx]
+    prof = gan_height_profile(g).astype(np.float32)
+    rho = np.empty((len(fams), nz, ny, nx), dtype=np.float32)
+    for q in range(len(fams)):
+        mask = ((grains % len(fams)) == q).astype(np.float32)
+        np.multiply(prof[:, None, None], mask[None], out=rho[q])
+    return ServingCase(g, t18[fams].copy(), b18[fams].copy(), rho)
 
 
 def random_problem(geom: Geometry, t: np.ndarray, b: np.ndarray, seed: int,

@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-reduced", action="store_true", help="skip the FP16-spectra measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency measurement")
     ap.add_argument("--serving-seconds", type=float, default=5.0)
+    ap.add_argument("--no-autotune", action="store_true", help="use the planner's default z schedule")
     return ap.parse_args()
 
 
@@ -363,7 +364,7 @@ def run_ours(args):
 
     p = W.CONFIGS[args.workload]()
     g = p.geom
-    ctx = dds.context_for(p, device=local)
+    ctx = dds.context_for(p, device=local, autotune=not args.no_autotune)
     q = ctx.query()
     rho = torch.from_numpy(np.ascontiguousarray(p.rho, dtype=np.float32)).cuda()
     sigma = torch.empty((6,) + g.shape, dtype=torch.float32, device="cuda")

@@ -108,6 +108,17 @@ int dds_set_option(dds_ctx *ctx, int key, double value);
  * default stream) and synchronises it before returning. */
 int dds_build_kernels(dds_ctx *ctx, void *cuda_stream);
 
+/* Autotuner (no counterpart in the paper; a schedule choice).  Call after
+ * dds_set_geometry / dds_set_families and before dds_build_kernels: times one full
+ * evaluation (synthetic densities and spectra; the schedule does not change the
+ * arithmetic's result beyond rounding) for every fused-z-pass schedule that applies
+ * -- the register kernel with each valid number of lanes per (kx, ky) column and the
+ * shared-memory kernel with each valid tile width -- and keeps the fastest for the
+ * build that follows.  Allocates temporary device memory and synchronises the
+ * stream.  *best_ms (host, may be NULL) receives the fastest evaluation time.
+ * DDS_OPT_Z_LANES set later overrides the choice. */
+int dds_autotune(dds_ctx *ctx, void *cuda_stream, float *best_ms);
+
 /* sigma = sum over families of G * rho (Eq. 10).  rho: device, [F][nz][ny][nx] in
  * m^-2, element type rho_dtype (DDS_F32; DDS_BF16 stores the density as bfloat16,
  * arithmetic stays FP32).  sigma: device, [6][nz][ny][nx] float32, Pa.  Both must be

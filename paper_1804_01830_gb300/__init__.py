@@ -31,7 +31,7 @@ DDS_OPT_Z_LANES = 2
 DDS_OPT_SPECTRA_FP16 = 3
 
 # Every symbol include/dds.h declares.
-EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option",
+EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option", "dds_autotune",
            "dds_build_kernels", "dds_stress", "dds_stress_multi", "dds_stress_stats", "dds_stress_batched",
            "dds_stress_noalloc",
            "dds_stress_host",
@@ -65,6 +65,7 @@ def load_library():
         "dds_set_families": ([vp, ctypes.c_int, dp, dp], ctypes.c_int),
         "dds_set_option": ([vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
         "dds_build_kernels": ([vp, vp], ctypes.c_int),
+        "dds_autotune": ([vp, vp, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "dds_stress": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
         "dds_stress_batched": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), ip,
                                 ctypes.POINTER(vp), vp], ctypes.c_int),
@@ -127,6 +128,13 @@ def dds_set_families(ctx, t, b):
 
 def dds_set_option(ctx, key: int, value: float):
     _check(ctx, load_library().dds_set_option(ctx, int(key), float(value)))
+
+
+def dds_autotune(ctx, stream=None) -> float:
+    """Pick the fastest fused-z schedule for this geometry (before build); returns its ms."""
+    ms = ctypes.c_float()
+    _check(ctx, load_library().dds_autotune(ctx, _stream_handle(stream), ctypes.byref(ms)))
+    return float(ms.value)
 
 
 def dds_build_kernels(ctx, stream=None):
@@ -251,6 +259,9 @@ class StressContext:
         dds_set_option(self.handle, key, value)
         return self
 
+    def autotune(self, stream=None) -> float:
+        return dds_autotune(self.handle, stream)
+
     def build_kernels(self, stream=None):
         dds_build_kernels(self.handle, stream)
         return self
@@ -324,7 +335,8 @@ class StressContext:
         return dds_launches_per_stress(self.handle)
 
 
-def context_for(problem, device: int = 0, n_near: float | None = None, stream=None) -> StressContext:
+def context_for(problem, device: int = 0, n_near: float | None = None, stream=None,
+                autotune: bool = False) -> StressContext:
     """Context set up and built for a ``workloads.Problem``-like object (geom, t, b)."""
     g = problem.geom
     ctx = StressContext(device)
@@ -332,5 +344,7 @@ def context_for(problem, device: int = 0, n_near: float | None = None, stream=No
     ctx.set_families(problem.t, problem.b)
     if n_near is not None:
         ctx.set_option(DDS_OPT_NEAR_RADIUS, n_near)
+    if autotune:
+        ctx.autotune(stream)
     ctx.build_kernels(stream)
     return ctx

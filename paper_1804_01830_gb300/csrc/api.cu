@@ -225,6 +225,11 @@ int make_plan(dds_ctx *ctx) {
       return fail(ctx, DDS_ERR_UNSUPPORTED, "z pass: %d lanes per column not available for pz %d", G, sh.pz);
   }
   // shared-memory z pass: fe field lines and three component lines per column
+  if (ctx->z_wz > 0) {                   // width fixed by the autotuner
+    sh.wz = ctx->z_wz;
+    ctx->shape = sh;
+    return DDS_OK;
+  }
   const size_t pref = 110 * 1024, cap = 220 * 1024;
   for (int pass = 0; pass < 2 && sh.wz == 0; ++pass) {
     for (int W : {64, 32, 16, 8, 4}) {
@@ -360,6 +365,11 @@ int dds_set_geometry(dds_ctx *ctx, int nx, int ny, int nz, double dx, double dy,
   ctx->mu = mu;
   ctx->nu = nu;
   ctx->has_geom = true;
+  if (ctx->tuned) {                      // a tuned schedule belongs to the old geometry
+    ctx->z_lanes = 0;
+    ctx->z_wz = 0;
+    ctx->tuned = false;
+  }
   invalidate(ctx);
   return DDS_OK;
 }
@@ -390,6 +400,11 @@ int dds_set_families(dds_ctx *ctx, int F, const double *t, const double *b) {
     return rc;
   }
   ctx->has_fam = true;
+  if (ctx->tuned) {
+    ctx->z_lanes = 0;
+    ctx->z_wz = 0;
+    ctx->tuned = false;
+  }
   invalidate(ctx);
   return DDS_OK;
 }
@@ -401,6 +416,8 @@ int dds_set_option(dds_ctx *ctx, int key, double value) {
       if (!(value == -1 || value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
         return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: z lanes must be -1, 0, 1, 2, 4 or 8");
       ctx->z_lanes = (int)value;
+      ctx->z_wz = 0;
+      ctx->tuned = false;
       invalidate(ctx);
       return DDS_OK;
     case DDS_OPT_SPECTRA_FP16:
@@ -436,6 +453,81 @@ int dds_build_kernels(dds_ctx *ctx, void *cuda_stream) {
   }
   ctx->built = true;
   ctx->err.clear();
+  return DDS_OK;
+}
+
+int dds_autotune(dds_ctx *ctx, void *cuda_stream, float *best_ms) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!ctx->has_geom || !ctx->has_fam)
+    return fail(ctx, DDS_ERR_NOT_READY, "autotune: set geometry and families first");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // candidate schedules of the fused z pass: (lanes, tile width)
+  ctx->z_lanes = 0;
+  ctx->z_wz = 0;
+  int rc = make_plan(ctx);
+  if (rc != DDS_OK) return rc;
+  const Shape base = ctx->shape;
+  std::vector<std::pair<int, int>> cand;
+  if (base.pz <= 64 && base.fe <= 4) {
+    for (int G : {1, 2, 4, 8}) {
+      const int E = base.pz / G;
+      if (base.pz % G == 0 && (E == 8 || E == 16) && base.M >= 32 / G) cand.push_back({G, 0});
+    }
+  }
+  for (int W : {4, 8, 16, 32, 64}) {
+    if (W > base.M || base.py % W != 0 || (W * base.pz > 2048 && W > 8)) continue;
+    const size_t fe = (size_t)std::max(base.fe, 1);
+    if ((sizeof(float2) * (fe + 3) + 2 * sizeof(float) * fe) * base.pz * W > 220 * 1024) continue;
+    cand.push_back({-1, W});
+  }
+  if (cand.empty()) return fail(ctx, DDS_ERR_UNSUPPORTED, "autotune: no z-pass schedule applies");
+  ctx->built = false;
+  const size_t N = (size_t)ctx->nx * ctx->ny * ctx->nz;
+  float *rho = nullptr, *sigma = nullptr;
+  cudaError_t err = cudaMalloc(&rho, sizeof(float) * N * ctx->F);
+  if (err == cudaSuccess) err = cudaMalloc(&sigma, sizeof(float) * N * 6);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  if (err == cudaSuccess) err = cudaMemsetAsync(rho, 0, sizeof(float) * N * ctx->F, s);
+  float best = 1e30f;
+  std::pair<int, int> pick = cand[0];
+  for (size_t i = 0; i < cand.size() && err == cudaSuccess && rc == DDS_OK; ++i) {
+    ctx->z_lanes = cand[i].first;
+    ctx->z_wz = cand[i].second;
+    rc = make_plan(ctx);
+    if (rc != DDS_OK) break;
+    if (ctx->shape.zreg_g != (cand[i].first > 0 ? cand[i].first : 0)) continue;   // planner declined
+    rc = alloc_buffers(ctx);
+    if (rc != DDS_OK) break;
+    const size_t vbytes = ctx->spectra_fp16 ? 2 : sizeof(float);
+    err = cudaMemsetAsync(ctx->kspec, 0, ctx->kspec_floats * vbytes, s);   // timing only: values are irrelevant
+    if (err == cudaSuccess && ctx->kscale) err = cudaMemsetAsync(ctx->kscale, 0, 6 * sizeof(float) * ctx->fe, s);
+    for (int w = 0; w < 2 && rc == DDS_OK && err == cudaSuccess; ++w) rc = enqueue_stress(ctx, rho, DDS_F32, sigma, s);
+    if (rc != DDS_OK || err != cudaSuccess) break;
+    err = cudaEventRecord(e0, s);
+    for (int r = 0; r < 5 && rc == DDS_OK && err == cudaSuccess; ++r) rc = enqueue_stress(ctx, rho, DDS_F32, sigma, s);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && rc == DDS_OK && ms / 5 < best) {
+      best = ms / 5;
+      pick = cand[i];
+    }
+  }
+  cudaFree(rho);
+  cudaFree(sigma);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  free_buffers(ctx);
+  ctx->z_lanes = pick.first;
+  ctx->z_wz = pick.second;
+  ctx->tuned = true;
+  if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "autotune: %s", cudaGetErrorString(err));
+  if (rc != DDS_OK) return rc;
+  if (best_ms) *best_ms = best;
   return DDS_OK;
 }
 

@@ -64,6 +64,8 @@ struct dds_ctx {
   double mu = 0, nu = 0;
   double n_near = 3.0;
   int z_lanes = 0;                      // fused z pass: 0 auto, -1 shared-memory kernel, G lanes/column
+  int z_wz = 0;                         // shared-memory z tile width chosen by dds_autotune (0: planner)
+  bool tuned = false;                   // z_lanes / z_wz were set by dds_autotune
   // families
   bool has_fam = false;
   int F = 0;

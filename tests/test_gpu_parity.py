@@ -315,3 +315,26 @@ def test_eq20_statistics_fused_into_the_evaluation(dds):
     assert np.abs(s2[0] - s).max() <= 1e-6 * np.abs(s).max()
     assert np.abs(s2[1] - 0.5 * s).max() <= 1e-5 * np.abs(s).max()
     ctx.close()
+
+
+# ------------------------------------------------------------- autotuner ---
+@pytest.mark.parametrize("case", ["thin", "tall"])
+def test_autotune_keeps_the_result(dds, case):
+    if case == "thin":
+        p = W.random_problem(W.Geometry(64, 48, 16, 0.5e-6, 0.5e-6, 0.2e-6), *[a[[0, 9]] for a in W.gan_families()],
+                             seed=61)
+    else:
+        p = W.gan_polycrystal(W.Geometry(32, 32, 40, 0.2e-6, 0.2e-6, 0.05e-6), 1e-6, seed=62)
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho, dtype=np.float32)).cuda()
+    plain = dds.context_for(p)
+    ref = plain.stress(rho).cpu().numpy()
+    tuned = dds.StressContext(0)
+    g = p.geom
+    tuned.set_geometry(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.mu, g.nu).set_families(p.t, p.b)
+    ms = tuned.autotune()
+    assert ms > 0
+    tuned.build_kernels()
+    got = tuned.stress(rho).cpu().numpy()
+    assert rel_l2_per_component(got, ref).max() <= 1e-6
+    plain.close()
+    tuned.close()

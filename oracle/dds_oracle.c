@@ -256,6 +256,27 @@ void orc_interaction(const orc_geom *g, int i, int j, int k, const double t[3],
   for (int c = 0; c < 6; ++c) out[c] = acc[c] / (double)M;
 }
 
+/* Sec. 4, Eq. 12 and Eq. 13: every replica of the source cell, r_i + (k Lx, l Ly, 0),
+ * contributes its coefficient at its own separation from the target. */
+void orc_interaction_pbc(const orc_geom *g, int i, int j, int k, const double t[3], const double b[3],
+                         double out[6]) {
+  const int n = g->n_shells;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int kk = -n; kk <= n; ++kk)
+    for (int ll = -n; ll <= n; ++ll) {
+      double s[6];
+      orc_interaction(g, i + kk * g->nx, j + ll * g->ny, k, t, b, s);
+      for (int c = 0; c < 6; ++c) acc[c] += s[c];
+    }
+  for (int c = 0; c < 6; ++c) out[c] = acc[c];
+}
+
+static void coefficient(const orc_geom *g, int i, int j, int k, const double t[3], const double b[3],
+                        double out[6]) {
+  if (g->n_shells > 0) orc_interaction_pbc(g, i, j, k, t, b, out);
+  else orc_interaction(g, i, j, k, t, b, out);
+}
+
 void orc_gtable(const orc_geom *g, const double t[3], const double b[3], double *out) {
   const int Ix = 2 * g->nx - 1, Iy = 2 * g->ny - 1, Iz = 2 * g->nz - 1;
   const long n = (long)Ix * Iy * Iz;
@@ -264,7 +285,7 @@ void orc_gtable(const orc_geom *g, const double t[3], const double b[3], double 
     const int i = (int)(q % Ix) - (g->nx - 1);
     const int j = (int)((q / Ix) % Iy) - (g->ny - 1);
     const int k = (int)(q / ((long)Ix * Iy)) - (g->nz - 1);
-    orc_interaction(g, i, j, k, t, b, out + 6 * q);
+    coefficient(g, i, j, k, t, b, out + 6 * q);
   }
 }
 
@@ -302,7 +323,7 @@ void orc_stress_direct(const orc_geom *g, int F, const double *t, const double *
             const long o = ((long)(tk - sk + nz - 1) * Iy + (tj - sj + ny - 1)) * Ix + (ti - si + nx - 1);
             for (int c = 0; c < 6; ++c) G[c] = table[6 * o + c];
           } else {
-            orc_interaction(g, ti - si, tj - sj, tk - sk, tf, bf, G);
+            coefficient(g, ti - si, tj - sj, tk - sk, tf, bf, G);
           }
           for (int c = 0; c < 6; ++c) acc[c] += G[c] * dens;
         }
@@ -323,7 +344,7 @@ void orc_stress_direct(const orc_geom *g, int F, const double *t, const double *
             const long o = ((long)(tk - sk + nz - 1) * Iy + (tj - sj + ny - 1)) * Ix + (ti - si + nx - 1);
             for (int c = 0; c < 6; ++c) G[c] = table[6 * o + c];
           } else {
-            orc_interaction(g, ti - si, tj - sj, tk - sk, tf, bf, G);
+            coefficient(g, ti - si, tj - sj, tk - sk, tf, bf, G);
           }
           a0 += G[0] * dens; a1 += G[1] * dens; a2 += G[2] * dens;
           a3 += G[3] * dens; a4 += G[4] * dens; a5 += G[5] * dens;

@@ -22,6 +22,8 @@ typedef struct {
   double h[3];     /* cell edge lengths dx, dy, dz (m) */
   double mu, nu;   /* shear modulus (Pa), Poisson ratio */
   double n_near;   /* near field: |offset| < n_near * max(h) is subdivided (Sec. 2.3) */
+  int n_shells;    /* in-plane periodic boundary conditions with replica shells |k|,|l| <= n_shells
+                      (Sec. 4, Eq. 12-13); 0: open boundary */
 } orc_geom;
 
 /* Eq. 4a-4c with Eq. 5: stress of a segment parallel to z from (0,0,zA) to
@@ -50,11 +52,16 @@ double orc_chord(const double h[3], const double t[3]);
 void orc_interaction(const orc_geom *g, int i, int j, int k, const double t[3],
                      const double b[3], double out[6]);
 
+/* Periodic boundary conditions in x and y (Sec. 4): F(Delta) = sum over replicas of the
+ * source cell, Eq. 13, |k|, |l| <= n_shells: sum_{k,l} G(i + k nx, j + l ny, k_z).  out[6]. */
+void orc_interaction_pbc(const orc_geom *g, int i, int j, int k, const double t[3], const double b[3],
+                         double out[6]);
+
 /* Full table over offsets i in [-(nx-1), nx-1] (same for j, k), layout
  * out[((k + nz-1) * (2ny-1) + (j + ny-1)) * (2nx-1) + (i + nx-1)][6]. */
 void orc_gtable(const orc_geom *g, const double t[3], const double b[3], double *out);
 
-/* Eq. 10 summed over families: sigma at the listed target cells (linear index
+/* Eq. 10 summed over families (Eq. 12 with n_shells > 0): sigma at the listed target cells (linear index
  * (k*ny + j)*nx + i) by direct summation over all source cells.
  * rho: [F][nz][ny][nx]; out: [ntargets][6].  use_table != 0 builds each family's
  * full table first (small grids), else coefficients are evaluated per pair. */

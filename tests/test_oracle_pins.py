@@ -343,3 +343,43 @@ def test_disk_example_magnitude_and_symmetry():
     # Sec. 2.3: halving the cell size does not noticeably change the result
     for name in cases:
         assert abs(peaks[(name, 80)] - peaks[(name, 40)]) < 0.05 * peaks[(name, 80)]
+
+
+# ------------------------------------------- periodic boundary conditions ----
+def test_replica_sum_equals_the_tiled_open_system():
+    """Eq. 12: summing the replicas of every source cell (|k|,|l| <= n) is the open-boundary
+    sum over the system tiled (2n+1) x (2n+1) times, seen from the central tile."""
+    g = W.Geometry(6, 5, 3, 1e-6, 1e-6, 0.25e-6, MU, NU)
+    t18, b18 = W.gan_families()
+    p = W.random_problem(g, t18[[0, 9]], b18[[0, 9]], seed=3)
+    n = 2
+    T = 2 * n + 1
+    pbc = oracle.stress_direct(g, p.t, p.b, p.rho, n_shells=n)
+    gt = W.Geometry(g.nx * T, g.ny * T, g.nz, g.dx, g.dy, g.dz, MU, NU)
+    tiled = np.tile(p.rho, (1, 1, T, T))
+    tg = [(k * gt.ny + j + n * g.ny) * gt.nx + i + n * g.nx
+          for k in range(g.nz) for j in range(g.ny) for i in range(g.nx)]
+    ref = oracle.stress_direct(gt, p.t, p.b, tiled, targets=tg)
+    assert rel(pbc, ref) < 1e-12
+
+
+def test_replica_shells_converge_as_the_paper_states():
+    gold = _read_golden("pbc_sec4.txt")
+    acc = float(gold["accuracy"])
+    g = W.Geometry(16, 16, 8, 1e-6, 1e-6, 1e-6, MU, NU)
+    rng = np.random.default_rng(0)
+    offs = list(zip(rng.integers(-15, 16, 30), rng.integers(-15, 16, 30), rng.integers(-7, 8, 30)))
+    for t, b in [([0, 0, 1], [BB, 0, 0]), ([0, 0, 1], [0, 0, BB]), (W.t_mixed(), [BB, 0, 1.6 * BB])]:
+        ref = np.array([oracle.interaction_pbc(g, *o, t, b, 80) for o in offs])
+        scale = np.abs(ref).max(axis=0)
+        for n in (int(gold["shells_low"]), int(gold["shells_high"])):
+            F = np.array([oracle.interaction_pbc(g, *o, t, b, n) for o in offs])
+            for c in range(6):
+                if scale[c] > 1e-12 * scale.max():
+                    assert np.abs(F[:, c] - ref[:, c]).max() < acc * scale[c], (t, b, n, c)
+
+
+def test_replica_table_is_odd():
+    g = W.Geometry(7, 6, 4, 1e-6, 1e-6, 0.25e-6, MU, NU)
+    tab = oracle.gtable(g, W.t_mixed(), (BB, 0.3 * BB, 1.6 * BB), n_shells=3)
+    assert rel(tab[::-1, ::-1, ::-1], -tab) < 1e-13

@@ -65,7 +65,13 @@ enum {
                               with that many lanes per (kx, ky) column (needs padded
                               z size <= 64 and <= 4 combined fields).  Same result up to
                               rounding; a tuning knob.  Invalidates built kernels. */
-  DDS_OPT_SPECTRA_FP16 = 3 /* 1: store the cached kernel spectra as FP16 with one FP32
+  DDS_OPT_PBC_SHELLS = 4,  /* in-plane periodic boundary conditions (Sec. 4): n > 0 makes
+                              every coefficient the sum over the replicas of the source
+                              cell, r_i + (k Lx, l Ly, 0) with |k|, |l| <= n (Eq. 12-13;
+                              the paper finds 15-20 shells accurate to 3%); the table
+                              build costs (2n + 1)^2 times more.  0 (default): open
+                              boundary.  Invalidates built kernels. */
+  DDS_OPT_SPECTRA_FP16 = 3,/* 1: store the cached kernel spectra as FP16 with one FP32
                               scale per (component, field) -- half the bytes of the
                               dominant pass; arithmetic stays FP32.  Error: about 1e-4
                               relative L2 against the FP64 sum (tested bound 5e-4)

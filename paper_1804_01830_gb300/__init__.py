@@ -29,6 +29,7 @@ DDS_BF16 = 1
 DDS_OPT_NEAR_RADIUS = 1
 DDS_OPT_Z_LANES = 2
 DDS_OPT_SPECTRA_FP16 = 3
+DDS_OPT_PBC_SHELLS = 4
 
 # Every symbol include/dds.h declares.
 EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option", "dds_autotune",

@@ -426,6 +426,12 @@ int dds_set_option(dds_ctx *ctx, int key, double value) {
       ctx->spectra_fp16 = value == 1;
       invalidate(ctx);
       return DDS_OK;
+    case DDS_OPT_PBC_SHELLS:
+      if (!(value >= 0 && value <= 1000) || value != (double)(int)value)
+        return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: replica shells must be an integer in [0, 1000]");
+      ctx->n_shells = (int)value;
+      invalidate(ctx);
+      return DDS_OK;
     case DDS_OPT_NEAR_RADIUS:
       if (!(value >= 0.0) || !isfinite(value))
         return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: near radius must be >= 0");
@@ -673,26 +679,20 @@ int dds_table_at(dds_ctx *ctx, const double t[3], const double b[3], long n, con
   double tu[3];
   for (int a = 0; a < 3; ++a) tu[a] = (fabs(tn - 1.0) <= 1e-15) ? t[a] : t[a] / tn;
   if (n == 0) return DDS_OK;
-  std::vector<unsigned char> near(n);
   for (long q = 0; q < n; ++q) {
     const int i = ijk_host[3 * q], j = ijk_host[3 * q + 1], k = ijk_host[3 * q + 2];
     if (abs(i) >= ctx->nx || abs(j) >= ctx->ny || abs(k) >= ctx->nz)
       return fail(ctx, DDS_ERR_INVALID_ARG, "table_at: offset (%d,%d,%d) outside the grid", i, j, k);
-    near[q] = ctx->n_near > 0.0 && is_near(ctx->h, ctx->n_near, i, j, k);
   }
   DeviceGuard guard(ctx->device);
   int *d_ijk = nullptr;
-  unsigned char *d_near = nullptr;
   double *d_out = nullptr;
   cudaError_t err = cudaMalloc(&d_ijk, sizeof(int) * 3 * n);
-  if (err == cudaSuccess) err = cudaMalloc(&d_near, n);
   if (err == cudaSuccess) err = cudaMalloc(&d_out, sizeof(double) * 6 * n);
   if (err == cudaSuccess) err = cudaMemcpy(d_ijk, ijk_host, sizeof(int) * 3 * n, cudaMemcpyHostToDevice);
-  if (err == cudaSuccess) err = cudaMemcpy(d_near, near.data(), n, cudaMemcpyHostToDevice);
-  if (err == cudaSuccess) err = launch_table_at(make_coef_geom(ctx), tu, b, n, d_ijk, d_near, d_out, 0);
+  if (err == cudaSuccess) err = launch_table_at(make_coef_geom(ctx), tu, b, n, d_ijk, d_out, 0);
   if (err == cudaSuccess) err = cudaMemcpy(out_host, d_out, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost);
   cudaFree(d_ijk);
-  cudaFree(d_near);
   cudaFree(d_out);
   if (err != cudaSuccess) {
     cudaGetLastError();

@@ -127,28 +127,59 @@ __device__ __forceinline__ double near_term(const CoefGeom &g, V3 base, int q, V
   return mult;
 }
 
+// Near field: |(i dx, j dy, k dz)|^2 < rn2, as ((x*x + y*y) + z*z) in round-to-nearest
+// double without contraction (the same decision as the plain IEEE expression).
+__device__ __forceinline__ bool near_dev(const CoefGeom &g, int i, int j, int k) {
+  const double x = __dmul_rn((double)i, g.h[0]), y = __dmul_rn((double)j, g.h[1]), z = __dmul_rn((double)k, g.h[2]);
+  return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)) < g.rn2;
+}
+
+// Coefficient of one source cell at cell offset (i, j, k): subdivided near the target
+// (mean over target subcells of the sum over source subcells), one segment otherwise.
+__device__ void coef_cell(const CoefGeom &g, int i, int j, int k, V3 t, V3 b, double out[6]) {
+  const V3 base = offset_pos(g, i, j, k);
+  if (!near_dev(g, i, j, k)) {
+    box_coef(base, g.h, t, b, g.mu, g.nu, out);
+    return;
+  }
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const int D = (2 * g.m[0] - 1) * (2 * g.m[1] - 1) * (2 * g.m[2] - 1);
+  for (int d = 0; d < D; ++d) {
+    double s[6];
+    const double mult = near_term(g, base, d, t, b, s);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] += mult * s[c];
+  }
+  const double iM = 1.0 / (double)(g.m[0] * g.m[1] * g.m[2]);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) out[c] = acc[c] * iM;
+}
+
+// With periodic boundary conditions (Sec. 4, Eq. 13): the sum over the replicas of the
+// source cell, r_i + (k Lx, l Ly, 0), |k|, |l| <= n_shells.
+__device__ void coef_any(const CoefGeom &g, int i, int j, int k, V3 t, V3 b, double out[6]) {
+  if (g.n_shells <= 0) {
+    coef_cell(g, i, j, k, t, b, out);
+    return;
+  }
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int kk = -g.n_shells; kk <= g.n_shells; ++kk)
+    for (int ll = -g.n_shells; ll <= g.n_shells; ++ll) {
+      double s[6];
+      coef_cell(g, i + kk * g.nx, j + ll * g.ny, k, t, b, s);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[c] += s[c];
+    }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) out[c] = acc[c];
+}
+
 // ---- coefficients at listed offsets (parity queries) ------------------------
-__global__ void k_table_at(CoefGeom g, V3 t, V3 b, long n, const int *ijk, const unsigned char *near,
-                           double *out) {
+__global__ void k_table_at(CoefGeom g, V3 t, V3 b, long n, const int *ijk, double *out) {
   const long q = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (q >= n) return;
-  const int i = ijk[3 * q], j = ijk[3 * q + 1], k = ijk[3 * q + 2];
-  const V3 base = offset_pos(g, i, j, k);
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  if (!near[q]) {
-    box_coef(base, g.h, t, b, g.mu, g.nu, acc);
-  } else {
-    const int D = (2 * g.m[0] - 1) * (2 * g.m[1] - 1) * (2 * g.m[2] - 1);
-    for (int d = 0; d < D; ++d) {
-      double s[6];
-      const double mult = near_term(g, base, d, t, b, s);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) acc[c] += mult * s[c];
-    }
-    const double iM = 1.0 / (double)(g.m[0] * g.m[1] * g.m[2]);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) acc[c] *= iM;
-  }
+  double acc[6];
+  coef_any(g, ijk[3 * q], ijk[3 * q + 1], ijk[3 * q + 2], t, b, acc);
 #pragma unroll
   for (int c = 0; c < 6; ++c) out[6 * q + c] = acc[c];
 }
@@ -166,7 +197,10 @@ __global__ void k_table_far(CoefGeom g, V3 t, V3 b, int nx, int ny, int nz, int 
   const int j = iy < ny ? iy : iy - py;
   const int k = iz < nz ? iz : iz - pz;
   double s[6] = {0, 0, 0, 0, 0, 0};
-  if (i > -nx && j > -ny && k > -nz) box_coef(offset_pos(g, i, j, k), g.h, t, b, g.mu, g.nu, s);
+  if (i > -nx && j > -ny && k > -nz) {
+    if (g.n_shells > 0) coef_any(g, i, j, k, t, b, s);     // replica sums include the near field
+    else box_coef(offset_pos(g, i, j, k), g.h, t, b, g.mu, g.nu, s);
+  }
 #pragma unroll
   for (int c = 0; c < 6; ++c) tab[c * P + idx] = s[c];
 }
@@ -385,6 +419,12 @@ CoefGeom coef_geom(const dds_ctx *ctx) {
   for (int a = 0; a < 3; ++a) g.hs[a] = ctx->h[a] / (double)g.m[a];
   g.mu = ctx->mu;
   g.nu = ctx->nu;
+  const double hmax = fmax(ctx->h[0], fmax(ctx->h[1], ctx->h[2]));
+  const double rn = ctx->n_near * hmax;
+  g.rn2 = rn * rn;
+  g.nx = ctx->nx;
+  g.ny = ctx->ny;
+  g.n_shells = ctx->n_shells;
   return g;
 }
 
@@ -392,12 +432,11 @@ CoefGeom coef_geom(const dds_ctx *ctx) {
 
 // -------------------------------------------------------------------------------
 cudaError_t launch_table_at(const CoefGeom &g, const double t[3], const double b[3], long n,
-                            const int *d_ijk, const unsigned char *d_near, double *d_out,
-                            cudaStream_t s) {
+                            const int *d_ijk, double *d_out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int nt = 128;
   k_table_at<<<(unsigned)((n + nt - 1) / nt), nt, 0, s>>>(g, v3(t[0], t[1], t[2]), v3(b[0], b[1], b[2]),
-                                                           n, d_ijk, d_near, d_out);
+                                                           n, d_ijk, d_out);
   return cudaGetLastError();
 }
 
@@ -411,8 +450,8 @@ int build_spectra(dds_ctx *ctx, cudaStream_t s) {
   const CoefGeom g = coef_geom(ctx);
 
   // near offsets (decided on the host, same expression as the definition)
-  std::vector<int> near;
-  if (ctx->n_near > 0.0) {
+  std::vector<int> near;                 // with replica shells the table kernel handles them
+  if (ctx->n_near > 0.0 && ctx->n_shells == 0) {
     double hmax = fmax(ctx->h[0], fmax(ctx->h[1], ctx->h[2]));
     int lim[3] = {ctx->nx - 1, ctx->ny - 1, ctx->nz - 1};
     for (int a = 0; a < 3; ++a) {

@@ -45,6 +45,9 @@ struct CoefGeom {
   double hs[3];       // subcell edges
   int m[3];           // subcells per axis
   double mu, nu;
+  double rn2;         // squared near-field radius (n_near * max h)^2
+  int nx, ny;         // grid (replica periods)
+  int n_shells;       // > 0: replica shells of the in-plane periodic boundary conditions
 };
 
 // Twiddle tables exp(-2 pi i k / P) for P = 16 .. 2048 (see dds_fft.cuh).
@@ -63,6 +66,7 @@ struct dds_ctx {
   double h[3] = {0, 0, 0};
   double mu = 0, nu = 0;
   double n_near = 3.0;
+  int n_shells = 0;                     // in-plane periodic boundary conditions (Sec. 4); 0: open
   int z_lanes = 0;                      // fused z pass: 0 auto, -1 shared-memory kernel, G lanes/column
   int z_wz = 0;                         // shared-memory z tile width chosen by dds_autotune (0: planner)
   bool tuned = false;                   // z_lanes / z_wz were set by dds_autotune
@@ -112,8 +116,7 @@ bool is_near(const double h[3], double n_near, int i, int j, int k);
 
 // FP64 coefficients at a list of offsets (device arrays), near flags per offset.
 cudaError_t launch_table_at(const CoefGeom &g, const double t[3], const double b[3], long n,
-                            const int *d_ijk, const unsigned char *d_near, double *d_out,
-                            cudaStream_t s);
+                            const int *d_ijk, double *d_out, cudaStream_t s);
 
 CoefGeom make_coef_geom(const dds_ctx *ctx);
 

@@ -161,7 +161,9 @@ def measured_peaks():
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("paper_1804_01830_gb300/csrc/stress.cu", "paper_1804_01830_gb300/csrc/dds_fft.cuh"):
+    for f in ("paper_1804_01830_gb300/csrc/stress.cu", "paper_1804_01830_gb300/csrc/dds_fft.cuh",
+              "paper_1804_01830_gb300/csrc/xpass.cuh", "paper_1804_01830_gb300/csrc/stress_common.cuh",
+              "paper_1804_01830_gb300/csrc/zpass_impl.cuh"):
         h.update((ROOT / f).read_bytes())
     return h.hexdigest()[:16]
 

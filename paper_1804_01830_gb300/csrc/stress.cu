@@ -18,137 +18,16 @@
 //   after y_fwd : main [e][z][ky][kx],     nyq [e][ky][z]
 //   after z     : main [c][z][ky][kx],     nyq [c][ky][z]
 //   after y_inv : main [c][z][y][kx],      nyq [c][y][z]
-// Every tile keeps its lines interleaved in shared memory (lanes across lines),
-// so global accesses are contiguous rows of W complex values.
+// The y passes keep W columns interleaved in shared memory (lanes across
+// columns), so global accesses are contiguous rows of W complex values; the x
+// passes (xpass.cuh) keep each line in the registers of a few threads.
 #include "stress_common.cuh"
+#include "xpass.cuh"
 
 namespace dds {
 
 namespace {
 
-
-// ---------------------------------------------------------------- x forward --
-template <int M, int W, int NT, bool BF16, bool DIRECT>
-__global__ void __launch_bounds__(NT) k_x_fwd(Shape sh, Collapse col, GroupList gl, const void *rho_v,
-                                              float2 *out_main, float2 *out_nyq, const float2 *tw) {
-  constexpr int LD = W + 1, PB = Plan<M>::r0;
-  constexpr int OWN = (W * (M / 2) + NT - 1) / NT;
-  extern __shared__ float2 smem[];
-  float2 *buf = smem;
-  const int tid = threadIdx.x;
-  const long L = (long)sh.ny * sh.nz;
-  const long N = L * sh.nx;
-  const long l0 = (long)blockIdx.x * W;
-  const int g = gl.g[blockIdx.y];
-  const int b = blockIdx.z;                       // density set of the batch
-  rho_v = BF16 ? (const void *)((const uint16_t *)rho_v + (long)b * sh.fin * L * sh.nx)
-               : (const void *)((const float *)rho_v + (long)b * sh.fin * L * sh.nx);
-  const int nxh = (sh.nx + 1) >> 1;
-  const bool even = (sh.nx & 1) == 0;
-  const float2 *twM = tw + tw_offset(M);
-  const float2 *tw2 = tw + tw_offset(2 * M);
-
-  // A group with one family (coefficient c) needs no combination: its line pairs are
-  // copied straight into the transposed tile and the spectrum is scaled by c.
-  // Otherwise every family of the group is read once and accumulated into all of
-  // the group's fields (at most three) in registers.
-  const int nd = col.nd[g];
-  float2 acc[DIRECT ? 1 : 3][OWN];
-  if constexpr (!DIRECT) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int i = 0; i < OWN; ++i) acc[d][i] = make_float2(0.f, 0.f);
-    for (int q = 0; q < col.nf[g]; ++q) {
-      const float c0 = col.coef[col.f0[g] + q][0], c1 = col.coef[col.f0[g] + q][1],
-                  c2 = col.coef[col.f0[g] + q][2];
-      const long fbase = (long)col.fam[col.f0[g] + q] * N + l0 * sh.nx;
-      float2 v[OWN];
-#pragma unroll
-      for (int i = 0; i < OWN; ++i) {
-        v[i] = make_float2(0.f, 0.f);
-        const int p = tid + i * NT;
-        if (p < W * nxh) {
-          const int w = p / nxh, n = p - w * nxh;
-          if (l0 + w < L) {
-            const long o = fbase + (long)w * sh.nx + 2 * n;
-            if (BF16) {
-              const uint16_t *r = (const uint16_t *)rho_v;
-              v[i].x = bf16_to_f32(r[o]);
-              v[i].y = (2 * n + 1 < sh.nx) ? bf16_to_f32(r[o + 1]) : 0.f;
-            } else {
-              const float *r = (const float *)rho_v;
-              if (even) {
-                v[i] = *reinterpret_cast<const float2 *>(r + o);
-              } else {
-                v[i].x = r[o];
-                v[i].y = (2 * n + 1 < sh.nx) ? r[o + 1] : 0.f;
-              }
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < OWN; ++i) {
-        acc[0][i].x = fmaf(c0, v[i].x, acc[0][i].x);
-        acc[0][i].y = fmaf(c0, v[i].y, acc[0][i].y);
-        acc[1][i].x = fmaf(c1, v[i].x, acc[1][i].x);
-        acc[1][i].y = fmaf(c1, v[i].y, acc[1][i].y);
-        acc[2][i].x = fmaf(c2, v[i].x, acc[2][i].x);
-        acc[2][i].y = fmaf(c2, v[i].y, acc[2][i].y);
-      }
-    }
-  }
-  for (int d = 0; d < nd; ++d) {
-    float scale_out = 1.0f;
-    if constexpr (DIRECT) {
-      scale_out = col.coef[col.f0[g]][0];
-      const float *r = (const float *)rho_v + (long)col.fam[col.f0[g]] * N + l0 * sh.nx;
-      for (int p = tid; p < W * nxh; p += NT) {
-        const int w = p / nxh, n = p - w * nxh;
-        if (l0 + w < L) cp_async8(&buf[tidx<LD, PB, W>(n, w)], r + (long)w * sh.nx + 2 * n);
-        else buf[tidx<LD, PB, W>(n, w)] = make_float2(0.f, 0.f);
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < OWN; ++i) {
-        const int p = tid + i * NT;
-        if (p < W * nxh) {
-          const int w = p / nxh, n = p - w * nxh;
-          if constexpr (!DIRECT) buf[tidx<LD, PB, W>(n, w)] = d == 0 ? acc[0][i] : (d == 1 ? acc[1][i] : acc[2][i]);
-        }
-      }
-    }
-    for (int p = W * nxh + tid; p < W * (M / 2); p += NT) {   // zero the tail of the non-zero half
-      const int w = p % W, n = p / W;
-      buf[tidx<LD, PB, W>(n, w)] = make_float2(0.f, 0.f);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    fft_tile<M, W, LD, NT, false, true, false, PB>(buf, twM, tid);
-    const int e = b * sh.fe + col.e0[g] + d;
-    for (int p = tid; p < W * M; p += NT) {
-      const int w = p / M, k = p - w * M;
-      const long line = l0 + w;
-      if (line >= L) continue;
-      const float2 a = buf[tidx<LD, PB, W>(k, w)];
-      const float2 c = buf[tidx<LD, PB, W>((M - k) & (M - 1), w)];
-      const float2 E = make_float2(0.5f * (a.x + c.x), 0.5f * (a.y - c.y));
-      const float2 O = make_float2(0.5f * (a.y + c.y), -0.5f * (a.x - c.x));
-      const float2 wk = __ldg(tw2 + k);
-      float2 X;
-      X.x = scale_out * (E.x + (wk.x * O.x - wk.y * O.y));
-      X.y = scale_out * (E.y + (wk.x * O.y + wk.y * O.x));
-      out_main[((long)e * L + line) * M + k] = X;
-      if (k == 0) {
-        const int z = (int)(line / sh.ny), y = (int)(line - (long)z * sh.ny);
-        out_nyq[((long)e * sh.ny + y) * sh.nz + z] =
-            make_float2(scale_out * (E.x - O.x), scale_out * (E.y - O.y));   // W^M = -1
-      }
-    }
-    __syncthreads();
-  }
-}
 
 // ------------------------------------------------------------- y passes -----
 // Forward: rows y < ny in, all py rows out.  Inverse: all py rows in, y < ny out.
@@ -221,88 +100,6 @@ __global__ void __launch_bounds__(NT) k_ypass(Shape sh, int nf, const float2 *in
 }
 
 
-// ---------------------------------------------------------------- x inverse --
-// stats != nullptr: also accumulate sum_x sigma^2 of every line into
-// stats[(set * 6 + c) * nz + z] (the per-height sums of Eq. 20).
-template <int M, int W, int NT>
-__global__ void __launch_bounds__(NT) k_x_inv(Shape sh, const float2 *in_main, const float2 *in_nyq,
-                                              float *sigma, const float2 *tw, double *stats) {
-  constexpr int LD = W + 1, PB = Plan<M>::r0;
-  extern __shared__ float2 smem[];
-  float2 *buf = smem;
-  float2 *xm = smem + tile_elems<M, LD, PB, W>();
-  const int tid = threadIdx.x;
-  const long L = 6L * sh.nb * sh.nz * sh.ny;
-  const long l0 = (long)blockIdx.x * W;
-  for (int p = tid; p < W * M; p += NT) {
-    const int w = p / M, k = p - w * M;
-    if (l0 + w < L) cp_async8(&buf[tidx<LD, PB, W>(k, w)], &in_main[(l0 + w) * M + k]);
-    else buf[tidx<LD, PB, W>(k, w)] = make_float2(0.f, 0.f);
-  }
-  if (tid < W) {
-    const long line = l0 + tid;
-    float2 v = make_float2(0.f, 0.f);
-    if (line < L) {
-      const long cz = line / sh.ny;
-      const int y = (int)(line - cz * sh.ny);
-      const int c = (int)(cz / sh.nz), z = (int)(cz - (long)c * sh.nz);
-      v = in_nyq[((long)c * sh.ny + y) * sh.nz + z];
-    }
-    xm[tid] = v;
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // Z[k] = (X[k] + conj X[M-k]) + i W^-k (X[k] - conj X[M-k]); pairs (k, M-k) per thread
-  const float2 *tw2 = tw + tw_offset(2 * M);
-  for (int p = tid; p < W * (M / 2 + 1); p += NT) {
-    const int w = p % W, k = p / W;
-    const float2 A = buf[tidx<LD, PB, W>(k, w)];
-    const float2 Bm = (k == 0) ? xm[w] : buf[tidx<LD, PB, W>(M - k, w)];   // X[M-k]
-    {
-      const float2 E = make_float2(A.x + Bm.x, A.y - Bm.y);
-      const float2 D = make_float2(A.x - Bm.x, A.y + Bm.y);
-      const float2 wk = __ldg(tw2 + k);                                  // W^k; use conj
-      const float2 O = make_float2(D.x * wk.x + D.y * wk.y, D.y * wk.x - D.x * wk.y);
-      buf[tidx<LD, PB, W>(k, w)] = make_float2(E.x - O.y, E.y + O.x);
-    }
-    if (k > 0 && k < M / 2) {
-      const float2 E = make_float2(Bm.x + A.x, Bm.y - A.y);
-      const float2 D = make_float2(Bm.x - A.x, Bm.y + A.y);
-      const float2 wk = __ldg(tw2 + (M - k));
-      const float2 O = make_float2(D.x * wk.x + D.y * wk.y, D.y * wk.x - D.x * wk.y);
-      buf[tidx<LD, PB, W>(M - k, w)] = make_float2(E.x - O.y, E.y + O.x);
-    }
-  }
-  __syncthreads();
-  fft_tile<M, W, LD, NT, true, false, true, PB>(buf, tw + tw_offset(M), tid);
-  const int nxh = (sh.nx + 1) >> 1;
-  const bool even = (sh.nx & 1) == 0;
-  float *lsum = reinterpret_cast<float *>(xm + W);     // per-line sums of squares (stats only)
-  if (stats != nullptr && tid < W) lsum[tid] = 0.f;
-  if (stats != nullptr) __syncthreads();
-  for (int p = tid; p < W * nxh; p += NT) {
-    const int w = p / nxh, n = p - w * nxh;
-    const long line = l0 + w;
-    if (line >= L) continue;
-    const float2 v = buf[tidx<LD, PB, W>(n, w)];
-    float *dst = sigma + line * sh.nx + 2 * n;
-    if (even) {
-      *reinterpret_cast<float2 *>(dst) = v;
-    } else {
-      dst[0] = v.x;
-      if (2 * n + 1 < sh.nx) dst[1] = v.y;
-    }
-    if (stats != nullptr) atomicAdd(&lsum[w], v.x * v.x + ((2 * n + 1 < sh.nx) ? v.y * v.y : 0.f));
-  }
-  if (stats != nullptr) {
-    __syncthreads();
-    if (tid < W && l0 + tid < L) {
-      const long line = l0 + tid;
-      atomicAdd(&stats[line / sh.ny], (double)lsum[tid]);   // line / ny = (set * 6 + c) * nz + z
-    }
-  }
-}
-
 // s = sqrt(sum / (nx ny)) for every (set, component, height).
 __global__ void k_stats_finish(const double *sums, long n, double inv_plane, float *s_out) {
   const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -314,30 +111,32 @@ __global__ void k_stats_finish(const double *sums, long n, double inv_plane, flo
 template <int M, bool BF16, bool DIRECT>
 cudaError_t launch_x_fwd_kind(const Shape &sh, const Collapse &col, const GroupList &gl, const void *rho,
                               float2 *om, float2 *on, const float2 *tw, cudaStream_t s) {
-  constexpr int W = XTile<M>::W, T = XTile<M>::NT;
-  const size_t smem = sizeof(float2) * tile_elems<M, W + 1, Plan<M>::r0, W>();
+  constexpr int LPB = xr::THREADS / (xr::FwdCfg<M>::R1 / 2);
   const long L = (long)sh.ny * sh.nz;
-  dim3 grid((unsigned)((L + W - 1) / W), gl.n, sh.nb);
-  cudaError_t err = prep(k_x_fwd<M, W, T, BF16, DIRECT>, smem);
+  dim3 grid((unsigned)((L + LPB - 1) / LPB), gl.n, sh.nb);
+  cudaError_t err = prep(xr::k_x_fwd_reg<M, BF16, DIRECT>, 0);
   if (err != cudaSuccess) return err;
-  k_x_fwd<M, W, T, BF16, DIRECT><<<grid, T, smem, s>>>(sh, col, gl, rho, om, on, tw);
+  xr::k_x_fwd_reg<M, BF16, DIRECT><<<grid, xr::THREADS, 0, s>>>(sh, col, gl, rho, om, on, tw);
   return cudaGetLastError();
 }
 
-// Groups with one family read that family straight into the tile (single-family
-// kernel); the others accumulate their families in registers.
+// Groups with one family and one field transform that family directly; the others
+// sum their families into each field first.
 template <int M>
 cudaError_t launch_x_fwd(const Shape &sh, const Collapse &col, const void *rho, bool bf16, float2 *om,
                          float2 *on, const float2 *tw, cudaStream_t s) {
   GroupList direct{}, accum{};
   for (int g = 0; g < col.ngroups; ++g) {
-    const bool d = !bf16 && (sh.nx % 2 == 0) && col.nf[g] == 1 && col.nd[g] == 1;
+    const bool d = col.nf[g] == 1 && col.nd[g] == 1;
     if (col.nd[g] == 0) continue;
     GroupList &gl = d ? direct : accum;
     gl.g[gl.n++] = g;
   }
   cudaError_t err = cudaSuccess;
-  if (direct.n > 0) err = launch_x_fwd_kind<M, false, true>(sh, col, direct, rho, om, on, tw, s);
+  if (direct.n > 0) {
+    err = bf16 ? launch_x_fwd_kind<M, true, true>(sh, col, direct, rho, om, on, tw, s)
+               : launch_x_fwd_kind<M, false, true>(sh, col, direct, rho, om, on, tw, s);
+  }
   if (err == cudaSuccess && accum.n > 0) {
     err = bf16 ? launch_x_fwd_kind<M, true, false>(sh, col, accum, rho, om, on, tw, s)
                : launch_x_fwd_kind<M, false, false>(sh, col, accum, rho, om, on, tw, s);
@@ -361,12 +160,11 @@ cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in
 template <int M>
 cudaError_t launch_x_inv(const Shape &sh, const float2 *im, const float2 *in, float *sigma, const float2 *tw,
                          cudaStream_t s, double *stats) {
-  constexpr int W = XTile<M>::W, T = XTile<M>::NT;
-  const size_t smem = sizeof(float2) * (tile_elems<M, W + 1, Plan<M>::r0, W>() + W) + sizeof(float) * W;
+  constexpr int LPB = xr::THREADS / (xr::InvCfg<M>::R2 / 2);
   const long L = 6L * sh.nb * sh.nz * sh.ny;
-  cudaError_t err = prep(k_x_inv<M, W, T>, smem);
+  cudaError_t err = prep(xr::k_x_inv_reg<M>, 0);
   if (err != cudaSuccess) return err;
-  k_x_inv<M, W, T><<<(unsigned)((L + W - 1) / W), T, smem, s>>>(sh, im, in, sigma, tw, stats);
+  xr::k_x_inv_reg<M><<<(unsigned)((L + LPB - 1) / LPB), xr::THREADS, 0, s>>>(sh, im, in, sigma, tw, stats);
   return cudaGetLastError();
 }
 
@@ -417,10 +215,10 @@ int stress_launch_count(const Shape &sh, const Collapse &col) {
   int direct = 0, accum = 0;
   for (int g = 0; g < col.ngroups; ++g) {
     if (col.nd[g] == 0) continue;
-    if ((sh.nx % 2 == 0) && col.nf[g] == 1 && col.nd[g] == 1) direct = 1;
+    if (col.nf[g] == 1 && col.nd[g] == 1) direct = 1;
     else accum = 1;
   }
-  return 4 + direct + accum;   // float32 densities; bfloat16 ones use the accumulating kernel
+  return 4 + direct + accum;
 }
 
 int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s, int nb,

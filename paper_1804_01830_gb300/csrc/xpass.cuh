@@ -1,0 +1,316 @@
+// Register-resident x passes: the real-to-complex FFT of the density lines and the
+// complex-to-real FFT of the stress lines (the first and last of the five passes).
+//
+// A line of the half spectrum has M = R1 * R2 complex points and is handled by T
+// threads.  Each thread keeps its share of the line in registers, so a line moves
+// through shared memory exactly once, between the two DFT stages of the four-step
+// factorisation
+//
+//   sum_n v[n] W^{kn},  n = n2 + R2 n1, k = k1 + R1 k2:
+//     stage 1: R1-point DFTs over n1 (one per column n2), times W_M^{n2 k1}
+//     stage 2: R2-point DFTs over n2 (one per row k1).
+//
+// Both passes also need, for every bin k, the bin M - k (the half-length real-FFT
+// identities).  The column (or row) that holds the mirror of column c is R - c, so
+// every thread owns a mirror pair of columns (inverse) or rows (forward) and the
+// identities are evaluated in registers.
+#pragma once
+#include "stress_common.cuh"
+
+namespace dds {
+namespace xr {
+
+// Inverse: R1 points per column, R2 columns, T = R2 / 2 threads per line, each
+// owning columns t and R2 - t (thread 0: columns 0 and R2 / 2, both self-mirrored).
+template <int M> struct InvCfg;
+template <> struct InvCfg<16>  { static constexpr int R1 = 4,  R2 = 4; };
+template <> struct InvCfg<32>  { static constexpr int R1 = 4,  R2 = 8; };
+template <> struct InvCfg<64>  { static constexpr int R1 = 8,  R2 = 8; };
+template <> struct InvCfg<128> { static constexpr int R1 = 8,  R2 = 16; };
+template <> struct InvCfg<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct InvCfg<512> { static constexpr int R1 = 16, R2 = 32; };
+
+// Forward: R1 points per column of which the first R1 / 2 are non-zero (the padded
+// half of the line), R2 columns, T = R1 / 2 threads per line, each owning rows t and
+// R1 - t of the second stage (thread 0: rows 0 and R1 / 2).
+template <int M> struct FwdCfg;
+template <> struct FwdCfg<16>  { static constexpr int R1 = 4,  R2 = 4; };
+template <> struct FwdCfg<32>  { static constexpr int R1 = 8,  R2 = 4; };
+template <> struct FwdCfg<64>  { static constexpr int R1 = 8,  R2 = 8; };
+template <> struct FwdCfg<128> { static constexpr int R1 = 16, R2 = 8; };
+template <> struct FwdCfg<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct FwdCfg<512> { static constexpr int R1 = 32, R2 = 16; };
+
+constexpr int THREADS = 128;
+
+// Shared-memory stride of one line: R rows of LD values, plus a shift that puts the
+// lines sharing a half-warp on different banks (conflict-free for every config).
+template <int T> __host__ __device__ constexpr int line_pad() { return T >= 16 ? 0 : T; }
+
+// ------------------------------------------------------------- x inverse ---
+// Z[k] = (X[k] + conj X[M-k]) + i conj(W_2M^k) (X[k] - conj X[M-k]); then
+// z = IDFT_M(Z) gives sigma[2n] = Re z[n], sigma[2n+1] = Im z[n].
+__device__ __forceinline__ float2 c2r_pre(float2 A, float2 Bm, float2 wk) {
+  const float2 E = make_float2(A.x + Bm.x, A.y - Bm.y);
+  const float2 D = make_float2(A.x - Bm.x, A.y + Bm.y);
+  const float2 O = make_float2(D.x * wk.x + D.y * wk.y, D.y * wk.x - D.x * wk.y);
+  return make_float2(E.x - O.y, E.y + O.x);
+}
+
+// stats != nullptr: also accumulate sum_x sigma^2 of every line into
+// stats[(set * 6 + c) * nz + z] (the per-height sums of Eq. 20).
+template <int M>
+__global__ void __launch_bounds__(THREADS)
+k_x_inv_reg(Shape sh, const float2 *__restrict__ in_main, const float2 *__restrict__ in_nyq,
+            float *__restrict__ sigma, const float2 *__restrict__ tw, double *stats) {
+  constexpr int R1 = InvCfg<M>::R1, R2 = InvCfg<M>::R2, T = R2 / 2, RPT = R1 / T;
+  constexpr int LPB = THREADS / T, LD = R1 + 1, S = R2 * LD + line_pad<T>();
+  static_assert(R1 * R2 == M && RPT >= 1 && RPT * T == R1, "x inverse config");
+  __shared__ float2 sm[LPB * S];
+  const int t = threadIdx.x % T, lw = threadIdx.x / T;
+  const long L = 6L * sh.nb * sh.nz * sh.ny;
+  const long line = (long)blockIdx.x * LPB + lw;
+  const bool live = line < L;
+  const bool t0 = t == 0;
+  const int ca = t, cb = t0 ? R2 / 2 : R2 - t;
+  const float2 *twM = tw + tw_offset(M);
+  const float2 *tw2 = tw + tw_offset(2 * M);
+
+  float2 a[R1], b[R1], xm = make_float2(0.f, 0.f);
+  if (live) {
+    const float2 *src = in_main + line * M;
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      a[n1] = __ldcs(src + ca + R2 * n1);
+      b[n1] = __ldcs(src + cb + R2 * n1);
+    }
+    if (t0) {
+      const long cz = line / sh.ny;
+      const int y = (int)(line - cz * sh.ny);
+      const int c = (int)(cz / sh.nz), z = (int)(cz - (long)c * sh.nz);
+      xm = in_nyq[((long)c * sh.ny + y) * sh.nz + z];
+    }
+  } else {
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) a[n1] = b[n1] = make_float2(0.f, 0.f);
+  }
+  // mirrors: X[M - k] of the bins k = ca + R2 n1 and k = cb + R2 n1
+  float2 za[R1], zb[R1];
+#pragma unroll
+  for (int n1 = 0; n1 < R1; ++n1) {
+    const float2 am = t0 ? (n1 == 0 ? xm : a[(R1 - n1) % R1]) : b[R1 - 1 - n1];
+    const float2 bm = t0 ? b[R1 - 1 - n1] : a[R1 - 1 - n1];
+    za[n1] = c2r_pre(a[n1], am, __ldg(tw2 + ca + R2 * n1));
+    zb[n1] = c2r_pre(b[n1], bm, __ldg(tw2 + cb + R2 * n1));
+  }
+  // stage 1: inverse R1-point DFTs of both columns, twiddle conj(W_M^{c m1})
+  dft_reg<R1, true>(za);
+  dft_reg<R1, true>(zb);
+  float2 *ls = sm + lw * S;
+#pragma unroll
+  for (int m1 = 0; m1 < R1; ++m1) {
+    if (m1 > 0) {
+      za[m1] = cmul_tw<true>(za[m1], __ldg(twM + ca * m1));
+      zb[m1] = cmul_tw<true>(zb[m1], __ldg(twM + cb * m1));
+    }
+    ls[ca * LD + m1] = za[m1];
+    ls[cb * LD + m1] = zb[m1];
+  }
+  __syncthreads();
+  // stage 2: rows m1 = t + T r, inverse R2-point DFTs; only the first half of the
+  // outputs (n = m1 + R1 m2 < M / 2) lie inside the unpadded line
+  const int nxh = (sh.nx + 1) >> 1;
+  const bool even = (sh.nx & 1) == 0;
+  float ssq = 0.f;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int m1 = t + T * r;
+    float2 y[R2];
+#pragma unroll
+    for (int c = 0; c < R2; ++c) y[c] = ls[c * LD + m1];
+    dft_reg<R2, true>(y);
+    if (live) {
+      float *dst = sigma + line * sh.nx;
+#pragma unroll
+      for (int m2 = 0; m2 < R2 / 2; ++m2) {
+        const int n = m1 + R1 * m2;
+        if (n < nxh) {
+          if (even) {
+            __stcs(reinterpret_cast<float2 *>(dst + 2 * n), y[m2]);
+            ssq += y[m2].x * y[m2].x + y[m2].y * y[m2].y;
+          } else {
+            dst[2 * n] = y[m2].x;
+            ssq += y[m2].x * y[m2].x;
+            if (2 * n + 1 < sh.nx) {
+              dst[2 * n + 1] = y[m2].y;
+              ssq += y[m2].y * y[m2].y;
+            }
+          }
+        }
+      }
+    }
+  }
+  if (stats != nullptr) {
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+    if (live && t0) atomicAdd(&stats[line / sh.ny], (double)ssq);
+  }
+}
+
+// ------------------------------------------------------------- x forward ---
+// Z = DFT_M(z), z[n] = x[2n] + i x[2n+1]; X[k] = E + W_2M^k O with
+// E = (Z[k] + conj Z[M-k]) / 2, O = -i (Z[k] - conj Z[M-k]) / 2, and
+// X[M] = E - O at k = 0.  Each field is scaled by `scale` on output.
+__device__ __forceinline__ float2 r2c_post(float2 a, float2 c, float2 wk, float scale) {
+  const float2 E = make_float2(0.5f * (a.x + c.x), 0.5f * (a.y - c.y));
+  const float2 O = make_float2(0.5f * (a.y + c.y), -0.5f * (a.x - c.x));
+  return make_float2(scale * (E.x + (wk.x * O.x - wk.y * O.y)), scale * (E.y + (wk.x * O.y + wk.y * O.x)));
+}
+
+// Complex pair (x[2n], x[2n+1]) of one density line (zero beyond nx).
+template <bool BF16>
+__device__ __forceinline__ float2 load_pair(const void *rho, long o, int n2x, int nx, bool even) {
+  if (BF16) {
+    const uint16_t *r = (const uint16_t *)rho;
+    return make_float2(bf16_to_f32(r[o]), n2x + 1 < nx ? bf16_to_f32(r[o + 1]) : 0.f);
+  }
+  const float *r = (const float *)rho;
+  if (even) return __ldcs(reinterpret_cast<const float2 *>(r + o));
+  return make_float2(r[o], n2x + 1 < nx ? r[o + 1] : 0.f);
+}
+
+// Groups with one family and one field (DIRECT) transform that family scaled by its
+// coefficient; the others sum coef * rho over the group's families for each field.
+template <int M, bool BF16, bool DIRECT>
+__global__ void __launch_bounds__(THREADS)
+k_x_fwd_reg(Shape sh, Collapse col, GroupList gl, const void *__restrict__ rho_v, float2 *__restrict__ out_main,
+            float2 *__restrict__ out_nyq, const float2 *__restrict__ tw) {
+  constexpr int R1 = FwdCfg<M>::R1, R2 = FwdCfg<M>::R2, T = R1 / 2, CPT = R2 / T, H = R1 / 2;
+  constexpr int LPB = THREADS / T, LD = R2 + 1, S = R1 * LD + line_pad<T>();
+  static_assert(R1 * R2 == M && CPT >= 1 && CPT * T == R2, "x forward config");
+  __shared__ float2 sm[LPB * S];
+  const int t = threadIdx.x % T, lw = threadIdx.x / T;
+  const long L = (long)sh.ny * sh.nz;
+  const long N = L * sh.nx;
+  const long line = (long)blockIdx.x * LPB + lw;
+  const bool live = line < L;
+  const bool t0 = t == 0;
+  const int g = gl.g[blockIdx.y];
+  const int bset = blockIdx.z;                       // density set of the batch
+  const long set_off = (long)bset * sh.fin * N;
+  const int nxh = (sh.nx + 1) >> 1;
+  const bool even = (sh.nx & 1) == 0;
+  const float2 *twM = tw + tw_offset(M);
+  const float2 *tw2 = tw + tw_offset(2 * M);
+  const int ra = t, rb = t0 ? R1 / 2 : R1 - t;
+  float2 *ls = sm + lw * S;
+
+  // stage-1 inputs z[n2 + R2 n1], n2 = t + T q, n1 < R1 / 2, of every field of the
+  // group: each family is read once and added into all fields (coef * rho).
+  constexpr int NDM = DIRECT ? 1 : 3;
+  const int nd = col.nd[g];
+  float2 acc[NDM][CPT][H];
+#pragma unroll
+  for (int d = 0; d < NDM; ++d)
+#pragma unroll
+    for (int q = 0; q < CPT; ++q)
+#pragma unroll
+      for (int n1 = 0; n1 < H; ++n1) acc[d][q][n1] = make_float2(0.f, 0.f);
+  const int nfam = DIRECT ? 1 : col.nf[g];
+  if (live) {
+#pragma unroll 2
+    for (int f = 0; f < nfam; ++f) {
+      const int fi = col.f0[g] + f;
+      const long base = set_off + (long)col.fam[fi] * N + line * sh.nx;
+      float2 v[CPT][H];
+#pragma unroll
+      for (int q = 0; q < CPT; ++q)
+#pragma unroll
+        for (int n1 = 0; n1 < H; ++n1) {
+          const int n = t + T * q + R2 * n1;
+          v[q][n1] = n < nxh ? load_pair<BF16>(rho_v, base + 2 * n, 2 * n, sh.nx, even) : make_float2(0.f, 0.f);
+        }
+      if (DIRECT) {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q)
+#pragma unroll
+          for (int n1 = 0; n1 < H; ++n1) acc[0][q][n1] = v[q][n1];
+      } else {
+#pragma unroll
+        for (int d = 0; d < NDM; ++d) {
+          const float cf = col.coef[fi][d];
+#pragma unroll
+          for (int q = 0; q < CPT; ++q)
+#pragma unroll
+            for (int n1 = 0; n1 < H; ++n1) {
+              acc[d][q][n1].x = fmaf(cf, v[q][n1].x, acc[d][q][n1].x);
+              acc[d][q][n1].y = fmaf(cf, v[q][n1].y, acc[d][q][n1].y);
+            }
+        }
+      }
+    }
+  }
+  const float dscale = DIRECT ? col.coef[col.f0[g]][0] : 1.f;
+
+#pragma unroll
+  for (int d = 0; d < NDM; ++d) {
+    if (d >= nd) break;
+    const float scale = dscale;
+    // stage 1: R1-point DFT of half-zero columns = two R1/2-point DFTs (even and odd
+    // outputs), then twiddle W_M^{n2 k1}
+    if (d > 0) __syncthreads();                      // previous field's stage 2 has read ls
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int n2 = t + T * q;
+      float2 ev[H], od[H];
+#pragma unroll
+      for (int n1 = 0; n1 < H; ++n1) {
+        ev[n1] = acc[d][q][n1];
+        od[n1] = rot_const<false>(acc[d][q][n1], n1, R1);
+      }
+      dft_reg<H, false>(ev);
+      dft_reg<H, false>(od);
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        const int k0 = 2 * j, k1 = 2 * j + 1;
+        float2 y0 = ev[j], y1 = od[j];
+        if (k0 > 0) y0 = cmul_tw<false>(y0, __ldg(twM + n2 * k0));
+        y1 = cmul_tw<false>(y1, __ldg(twM + n2 * k1));
+        ls[k0 * LD + n2] = y0;
+        ls[k1 * LD + n2] = y1;
+      }
+    }
+    __syncthreads();
+    // stage 2: rows ra and rb, R2-point DFTs -> Z[r + R1 k2]
+    float2 ya[R2], yb[R2];
+#pragma unroll
+    for (int c = 0; c < R2; ++c) {
+      ya[c] = ls[ra * LD + c];
+      yb[c] = ls[rb * LD + c];
+    }
+    dft_reg<R2, false>(ya);
+    dft_reg<R2, false>(yb);
+    if (live) {
+      const int e = bset * sh.fe + col.e0[g] + d;
+      float2 *dst = out_main + ((long)e * L + line) * M;
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) {
+        const float2 am = t0 ? ya[(R2 - k2) % R2] : yb[R2 - 1 - k2];
+        const float2 bm = t0 ? yb[R2 - 1 - k2] : ya[R2 - 1 - k2];
+        const int ka = ra + R1 * k2, kb = rb + R1 * k2;
+        __stcs(dst + ka, r2c_post(ya[k2], am, __ldg(tw2 + ka), scale));
+        __stcs(dst + kb, r2c_post(yb[k2], bm, __ldg(tw2 + kb), scale));
+      }
+      if (t0) {
+        const int z = (int)(line / sh.ny), y = (int)(line - (long)z * sh.ny);
+        const float2 a0 = ya[0];
+        const float2 E = make_float2(0.5f * (a0.x + a0.x), 0.5f * (a0.y - a0.y));
+        const float2 O = make_float2(0.5f * (a0.y + a0.y), -0.5f * (a0.x - a0.x));
+        out_nyq[((long)e * sh.ny + y) * sh.nz + z] = make_float2(scale * (E.x - O.x), scale * (E.y - O.y));
+      }
+    }
+  }
+}
+
+}  // namespace xr
+}  // namespace dds

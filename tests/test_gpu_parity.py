@@ -113,6 +113,12 @@ def test_gaussian_disk_32_full(dds):
     ((16, 64, 3), (0.5e-6, 0.5e-6, 0.2e-6), [1, 4, 6, 13, 17], 3),
     ((64, 16, 16), (0.3e-6, 0.3e-6, 0.3e-6), [5, 10], 4),                # cubic cells (no subdivision)
     ((7, 1, 1), (1e-6, 1e-6, 1e-6), [3, 12], 6),                         # a single line
+    ((101, 12, 4), (0.2e-6, 0.2e-6, 0.05e-6), [0, 9], 7),                 # M = 128, odd nx
+    ((128, 9, 3), (0.5e-6, 0.5e-6, 0.2e-6), [4, 11, 16], 8),              # M = 128, full half line
+    ((129, 6, 3), (0.2e-6, 0.2e-6, 0.05e-6), [2], 9),                     # M = 256, odd nx, one family
+    ((250, 5, 2), (1e-6, 1e-6, 0.25e-6), [1, 6, 12], 10),                 # M = 256
+    ((300, 3, 2), (0.5e-6, 0.5e-6, 0.2e-6), [7, 14], 11),                 # M = 512
+    ((17, 5, 4), (0.2e-6, 0.2e-6, 0.05e-6), [5], 12),                     # M = 32, odd nx, one family
 ])
 def test_random_densities_vs_direct_sum(dds, shape, cells, fams, seed):
     g = W.Geometry(*shape, *cells)
@@ -182,8 +188,10 @@ def test_linearity_at_full_size(dds):
     ctx.close()
 
 
-def test_bf16_density_storage(dds):
-    p = W.random_problem(W.Geometry(24, 20, 8, 0.2e-6, 0.2e-6, 0.05e-6), *[a[[0, 9]] for a in W.gan_families()],
+@pytest.mark.parametrize("shape,fams", [((24, 20, 8), [0, 9]),              # one family per group
+                                        ((33, 10, 5), [0, 1, 2, 9, 10])])    # summed families, odd nx
+def test_bf16_density_storage(dds, shape, fams):
+    p = W.random_problem(W.Geometry(*shape, 0.2e-6, 0.2e-6, 0.05e-6), *[a[fams] for a in W.gan_families()],
                          seed=11)
     got = gpu_stress(dds, p, dtype=torch.bfloat16)
     rho_bf16 = torch.from_numpy(p.rho.astype(np.float32)).to(torch.bfloat16).float().double().numpy()

@@ -209,6 +209,18 @@ int dds_profile_enable(dds_ctx *ctx, int enable);
  * the records. */
 int dds_profile_read(dds_ctx *ctx, int max_steps, float *ms_out, int *n_steps, int *n_passes);
 
+/* Bounded device waits (no counterpart in the paper).  The passes that stage their
+ * input with bulk asynchronous copies wait for each copy on a shared-memory
+ * barrier; a wait that has not completed after one second of device time gives
+ * up, the kernel skips its remaining work (its output is then incomplete) and
+ * records the event in a status word of the device.  This returns DDS_OK if no
+ * wait has given up on `cuda_device` since the last reset, DDS_ERR_TIMEOUT if
+ * one has, DDS_ERR_INVALID_ARG for a bad device, DDS_ERR_CUDA if the word cannot
+ * be read.  It reads the word with a synchronous copy, so it sees the kernels that
+ * have finished: synchronise the streams of interest first.  reset != 0 clears
+ * the word after reading it.  Needs no context. */
+int dds_device_status(int cuda_device, int reset);
+
 /* Last error message of this context (never NULL; "" if none). */
 const char *dds_last_error(const dds_ctx *ctx);
 

@@ -37,7 +37,7 @@ EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option
            "dds_stress_noalloc",
            "dds_stress_host",
            "dds_table_at", "dds_query", "dds_launches_per_stress", "dds_profile_enable",
-           "dds_profile_read", "dds_last_error", "dds_destroy")
+           "dds_profile_read", "dds_device_status", "dds_last_error", "dds_destroy")
 
 PASS_NAMES = ("x_fwd", "y_fwd", "z_fused", "y_inv", "x_inv")
 
@@ -79,6 +79,7 @@ def load_library():
         "dds_launches_per_stress": ([vp], ctypes.c_int),
         "dds_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
         "dds_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ip, ip], ctypes.c_int),
+        "dds_device_status": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "dds_last_error": ([vp], ctypes.c_char_p),
         "dds_destroy": ([vp], None),
     }
@@ -214,6 +215,11 @@ def dds_profile_read(ctx, max_steps: int) -> np.ndarray:
                                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                                 ctypes.byref(ns), ctypes.byref(npass)))
     return out[: ns.value, : npass.value]
+
+
+def dds_device_status(device: int = 0, reset: bool = False) -> int:
+    """DDS_OK, or DDS_ERR_TIMEOUT if a bounded device wait gave up since the last reset."""
+    return int(load_library().dds_device_status(int(device), int(bool(reset))))
 
 
 def dds_last_error(ctx) -> str:

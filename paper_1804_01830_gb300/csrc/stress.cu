@@ -21,12 +21,56 @@
 // The y passes keep W columns interleaved in shared memory (lanes across
 // columns), so global accesses are contiguous rows of W complex values; the x
 // passes (xpass.cuh) keep each line in the registers of a few threads.
+#include <algorithm>
+#include <mutex>
+
 #include "stress_common.cuh"
 #include "xpass.cuh"
 
 namespace dds {
 
+// Set by a bounded device wait that gave up (bulk.cuh); read by dds_device_status.
+__device__ int g_wait_status;
+
 namespace {
+
+constexpr int MAX_DEV = 64;
+
+// Per device: SM count and the address of g_wait_status (looked up once).
+struct DevInfo {
+  int sms = 0;
+  int *status = nullptr;
+};
+
+cudaError_t dev_info(DevInfo *out) {
+  static std::mutex mu;
+  static DevInfo info[MAX_DEV];
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= MAX_DEV) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!info[dev].status) {
+    err = cudaDeviceGetAttribute(&info[dev].sms, cudaDevAttrMultiProcessorCount, dev);
+    void *p = nullptr;
+    if (err == cudaSuccess) err = cudaGetSymbolAddress(&p, g_wait_status);
+    if (err != cudaSuccess) return err;
+    info[dev].status = static_cast<int *>(p);
+  }
+  *out = info[dev];
+  return cudaSuccess;
+}
+
+// Persistent grid: as many CTAs as fit on the device at once, at most one per tile.
+template <typename K>
+cudaError_t persistent_grid(K kernel, int threads, size_t smem, long tiles, const DevInfo &di, unsigned *grid) {
+  int per_sm = 0;
+  const cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  if (err != cudaSuccess) return err;
+  const long g = std::max(1L, std::min(tiles, (long)std::max(per_sm, 1) * di.sms));
+  *grid = (unsigned)g;
+  return cudaSuccess;
+}
 
 
 // ------------------------------------------------------------- y passes -----
@@ -157,14 +201,30 @@ cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in
 }
 
 
+// Lines of up to 256 points: persistent kernel with bulk-copied tiles (GaN layer
+// 256x256x128: 185 -> 155 us); 512 points: the plain register kernel, which keeps
+// four CTAs per SM instead of three (radial disk 512x512x16: 82 us against 90).
 template <int M>
 cudaError_t launch_x_inv(const Shape &sh, const float2 *im, const float2 *in, float *sigma, const float2 *tw,
                          cudaStream_t s, double *stats) {
-  constexpr int LPB = xr::THREADS / (xr::InvCfg<M>::R2 / 2);
+  if constexpr (M >= 512) {
+    constexpr int LPB = xr::THREADS / (xr::InvCfg<M>::R2 / 2);
+    const long L = 6L * sh.nb * sh.nz * sh.ny;
+    cudaError_t err = prep(xr::k_x_inv_reg<M>, 0);
+    if (err != cudaSuccess) return err;
+    xr::k_x_inv_reg<M><<<(unsigned)((L + LPB - 1) / LPB), xr::THREADS, 0, s>>>(sh, im, in, sigma, tw, stats);
+    return cudaGetLastError();
+  }
+  using C = xr::InvTma<M>;
   const long L = 6L * sh.nb * sh.nz * sh.ny;
-  cudaError_t err = prep(xr::k_x_inv_reg<M>, 0);
+  DevInfo di;
+  cudaError_t err = dev_info(&di);
+  if (err == cudaSuccess) err = prep(xr::k_x_inv_tma<M>, C::SMEM);
+  unsigned grid = 0;
+  if (err == cudaSuccess)
+    err = persistent_grid(xr::k_x_inv_tma<M>, xr::THREADS, C::SMEM, (L + C::LPB - 1) / C::LPB, di, &grid);
   if (err != cudaSuccess) return err;
-  xr::k_x_inv_reg<M><<<(unsigned)((L + LPB - 1) / LPB), xr::THREADS, 0, s>>>(sh, im, in, sigma, tw, stats);
+  xr::k_x_inv_tma<M><<<grid, xr::THREADS, C::SMEM, s>>>(sh, im, in, sigma, tw, stats, di.status);
   return cudaGetLastError();
 }
 
@@ -280,3 +340,18 @@ int enqueue_stress_buffers(dds_ctx *ctx, const void *rho, int rho_dtype, float *
 }
 
 }  // namespace dds
+
+extern "C" int dds_device_status(int cuda_device, int reset) {
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) return DDS_ERR_CUDA;
+  if (prev != cuda_device && cudaSetDevice(cuda_device) != cudaSuccess) return DDS_ERR_INVALID_ARG;
+  int v = 0;
+  cudaError_t err = cudaMemcpyFromSymbol(&v, dds::g_wait_status, sizeof(int));
+  if (err == cudaSuccess && reset && v != 0) {
+    const int zero = 0;
+    err = cudaMemcpyToSymbol(dds::g_wait_status, &zero, sizeof(int));
+  }
+  if (prev != cuda_device) cudaSetDevice(prev);
+  if (err != cudaSuccess) return DDS_ERR_CUDA;
+  return v == 0 ? DDS_OK : DDS_ERR_TIMEOUT;
+}

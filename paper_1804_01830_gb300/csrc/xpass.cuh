@@ -15,6 +15,7 @@
 // every thread owns a mirror pair of columns (inverse) or rows (forward) and the
 // identities are evaluated in registers.
 #pragma once
+#include "bulk.cuh"
 #include "stress_common.cuh"
 
 namespace dds {
@@ -154,6 +155,168 @@ k_x_inv_reg(Shape sh, const float2 *__restrict__ in_main, const float2 *__restri
 #pragma unroll
     for (int o = T / 2; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
     if (live && t0) atomicAdd(&stats[line / sh.ny], (double)ssq);
+  }
+}
+
+// Persistent form of the inverse pass: each CTA walks the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; the LPB input lines of a tile are contiguous and
+// arrive in one bulk copy (TMA) into one of two shared-memory slots, issued two
+// tiles ahead, so the copy of the next tile overlaps the transforms of this one.
+// A slot, once its lines are in registers, serves as the tile's transpose buffer.
+template <int M> struct InvTma {
+  static constexpr int R1 = InvCfg<M>::R1, R2 = InvCfg<M>::R2, T = R2 / 2;
+  static constexpr int LPB = THREADS / T, S = R2 * (R1 + 1) + line_pad<T>();
+  static constexpr int SLOT = (LPB * M > LPB * S ? LPB * M : LPB * S);       // float2 per slot
+  static constexpr size_t SMEM = sizeof(float2) * 2 * SLOT + 2 * sizeof(uint64_t);
+};
+
+__device__ __forceinline__ long nyq_index(const Shape &sh, long line) {
+  const long cz = line / sh.ny;
+  const int y = (int)(line - cz * sh.ny);
+  const int c = (int)(cz / sh.nz), z = (int)(cz - (long)c * sh.nz);
+  return ((long)c * sh.ny + y) * sh.nz + z;
+}
+
+template <int M>
+__global__ void __launch_bounds__(THREADS)
+k_x_inv_tma(Shape sh, const float2 *__restrict__ in_main, const float2 *__restrict__ in_nyq,
+            float *__restrict__ sigma, const float2 *__restrict__ tw, double *stats, int *status) {
+  using C = InvTma<M>;
+  constexpr int R1 = C::R1, R2 = C::R2, T = C::T, RPT = R1 / T, LPB = C::LPB, LD = R1 + 1, S = C::S;
+  static_assert(R1 * R2 == M && RPT >= 1 && RPT * T == R1, "x inverse config");
+  extern __shared__ __align__(16) float2 dsm[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(dsm + 2 * C::SLOT);
+  const int t = threadIdx.x % T, lw = threadIdx.x / T;
+  const bool t0 = t == 0;
+  const int ca = t, cb = t0 ? R2 / 2 : R2 - t;
+  const long L = 6L * sh.nb * sh.nz * sh.ny;
+  const long ntiles = (L + LPB - 1) / LPB;
+  const long stride = gridDim.x;
+  const float2 *twM = tw + tw_offset(M);
+  const float2 *tw2 = tw + tw_offset(2 * M);
+  const int nxh = (sh.nx + 1) >> 1;
+  const bool even = (sh.nx & 1) == 0;
+
+  auto issue = [&](long tile, int s) {        // one thread: bulk copy of a tile into slot s
+    const long l0 = tile * LPB;
+    const unsigned bytes = (unsigned)(min((long)LPB, L - l0) * M * sizeof(float2));
+    mbar_arrive_expect_tx(&bar[s], bytes);
+    bulk_g2s(dsm + s * C::SLOT, in_main + l0 * M, bytes, &bar[s]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // thread 0 only: copies issued and not yet waited for, and the barrier phase
+  // (parity) each will complete; use j of slot j & 1 completes phase (j >> 1) & 1
+  bool pending[2] = {false, false};
+  unsigned pend_par[2] = {0u, 0u};
+  if (threadIdx.x == 0) {
+    if (blockIdx.x < ntiles) { issue(blockIdx.x, 0); pending[0] = true; }
+    if (blockIdx.x + stride < ntiles) { issue(blockIdx.x + stride, 1); pending[1] = true; }
+  }
+  float2 xm_next = make_float2(0.f, 0.f);
+  {
+    const long line = (long)blockIdx.x * LPB + lw;
+    if (t0 && blockIdx.x < ntiles && line < L) xm_next = in_nyq[nyq_index(sh, line)];
+  }
+  bool ok = true;
+  for (long i = 0;; ++i) {
+    const long tile = blockIdx.x + i * stride;
+    if (tile >= ntiles) break;
+    const int s = (int)(i & 1);
+    const unsigned parity = (unsigned)((i >> 1) & 1);
+    float2 *buf = dsm + s * C::SLOT;
+    const long line = tile * LPB + lw;
+    const bool live = line < L;
+    const float2 xm = xm_next;
+    {
+      const long nline = (tile + stride) * LPB + lw;
+      xm_next = (t0 && tile + stride < ntiles && nline < L) ? in_nyq[nyq_index(sh, nline)] : make_float2(0.f, 0.f);
+    }
+    ok = __syncthreads_and(mbar_wait_bounded(&bar[s], parity, status));
+    if (!ok) break;
+    if (threadIdx.x == 0) pending[s] = false;
+    float2 a[R1], b[R1];
+    const float2 *src = buf + lw * M;
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      a[n1] = src[ca + R2 * n1];
+      b[n1] = src[cb + R2 * n1];
+    }
+    __syncthreads();                          // raw lines read: the slot becomes the transpose buffer
+    float2 za[R1], zb[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      const float2 am = t0 ? (n1 == 0 ? xm : a[(R1 - n1) % R1]) : b[R1 - 1 - n1];
+      const float2 bm = t0 ? b[R1 - 1 - n1] : a[R1 - 1 - n1];
+      za[n1] = c2r_pre(a[n1], am, __ldg(tw2 + ca + R2 * n1));
+      zb[n1] = c2r_pre(b[n1], bm, __ldg(tw2 + cb + R2 * n1));
+    }
+    dft_reg<R1, true>(za);
+    dft_reg<R1, true>(zb);
+    float2 *ls = buf + lw * S;
+#pragma unroll
+    for (int m1 = 0; m1 < R1; ++m1) {
+      if (m1 > 0) {
+        za[m1] = cmul_tw<true>(za[m1], __ldg(twM + ca * m1));
+        zb[m1] = cmul_tw<true>(zb[m1], __ldg(twM + cb * m1));
+      }
+      ls[ca * LD + m1] = za[m1];
+      ls[cb * LD + m1] = zb[m1];
+    }
+    __syncthreads();
+    float ssq = 0.f;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int m1 = t + T * r;
+      float2 y[R2];
+#pragma unroll
+      for (int c = 0; c < R2; ++c) y[c] = ls[c * LD + m1];
+      dft_reg<R2, true>(y);
+      if (live) {
+        float *dst = sigma + line * sh.nx;
+#pragma unroll
+        for (int m2 = 0; m2 < R2 / 2; ++m2) {
+          const int n = m1 + R1 * m2;
+          if (n < nxh) {
+            if (even) {
+              __stcs(reinterpret_cast<float2 *>(dst + 2 * n), y[m2]);
+              ssq += y[m2].x * y[m2].x + y[m2].y * y[m2].y;
+            } else {
+              dst[2 * n] = y[m2].x;
+              ssq += y[m2].x * y[m2].x;
+              if (2 * n + 1 < sh.nx) {
+                dst[2 * n + 1] = y[m2].y;
+                ssq += y[m2].y * y[m2].y;
+              }
+            }
+          }
+        }
+      }
+    }
+    if (stats != nullptr) {
+#pragma unroll
+      for (int o = T / 2; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+      if (live && t0) atomicAdd(&stats[line / sh.ny], (double)ssq);
+    }
+    __syncthreads();                          // slot free: refill it two tiles ahead
+    if (threadIdx.x == 0 && tile + 2 * stride < ntiles) {
+      fence_proxy_async_smem();
+      issue(tile + 2 * stride, s);
+      pending[s] = true;
+      pend_par[s] = (unsigned)(((i + 2) >> 1) & 1);
+    }
+  }
+  if (!ok && threadIdx.x == 0) {              // gave up: let copies still in flight land first
+    for (int s = 0; s < 2; ++s)
+      if (pending[s]) {
+        const unsigned long long t0ns = global_ns();
+        while (!mbar_try_wait(&bar[s], pend_par[s]) && global_ns() - t0ns < WAIT_LIMIT_NS) {
+        }
+      }
   }
 }
 

@@ -346,3 +346,13 @@ def test_autotune_keeps_the_result(dds, case):
     assert rel_l2_per_component(got, ref).max() <= 1e-6
     plain.close()
     tuned.close()
+
+
+def test_no_bounded_wait_gave_up(dds):
+    # the bulk-copy waits of the x passes record a timeout in the device status word
+    p = W.random_problem(W.Geometry(200, 40, 6, 0.2e-6, 0.2e-6, 0.05e-6), *[a[[0, 9]] for a in W.gan_families()],
+                         seed=3)
+    got = gpu_stress(dds, p)
+    assert np.isfinite(got).all()
+    torch.cuda.synchronize()
+    assert dds.dds_device_status(0) == dds.DDS_OK

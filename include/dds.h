@@ -209,6 +209,27 @@ int dds_profile_enable(dds_ctx *ctx, int enable);
  * the records. */
 int dds_profile_read(dds_ctx *ctx, int max_steps, float *ms_out, int *n_steps, int *n_passes);
 
+/* Free-surface relaxation (Sec. 5, Eqs. 14-18).  The stress sigma_dis of the
+ * dislocations in an infinite medium (for instance the output of dds_stress)
+ * loads a film whose top and bottom faces (the centres of the first and last
+ * layers) are free and whose sides are periodic.  The displacement u relaxes by
+ * n_steps explicit steps of Eq. 17,
+ *     u <- u + dt (A grad div u - B rot rot u + f),  f_a = sum_b d sigma_dis_ab / db,
+ * A = E(1-nu)/((1+nu)(1-2nu)), B = E/(2(1+nu)), dt = min(dx,dy,dz)^2 / (5A - 3B),
+ * with the traction-free conditions of Eq. 16c held by ghost layers (Eq. 18b).
+ * Central differences; d sigma_dis/dz one-sided (second order) on the surface
+ * layers.  Arithmetic in FP32.
+ *   sigma_dis  device, [6][nz][ny][nx] FP32, Pa (xx, yy, zz, xy, xz, yz); read only.
+ *   u          device, [3][nz][ny][nx] FP32, metres (x, y, z); the starting state
+ *              (zeros for a fresh relaxation), overwritten by the state after
+ *              n_steps, so calls continue where the last one stopped.
+ *   sigma_tot  device, [6][nz][ny][nx] FP32, or NULL: sigma_dis + sigma(u), the
+ *              stress of the free film (Hooke's law on central differences).
+ * Needs only the geometry (dds_set_geometry), nz >= 2 (DDS_ERR_UNSUPPORTED
+ * otherwise); n_steps >= 0.  Allocates 6 nx ny nz + 6 nx ny floats of work space
+ * on first use (DDS_ERR_OOM).  Asynchronous on `cuda_stream`. */
+int dds_relax(dds_ctx *ctx, const float *sigma_dis, float *u, int n_steps, float *sigma_tot, void *cuda_stream);
+
 /* Bounded device waits (no counterpart in the paper).  The passes that stage their
  * input with bulk asynchronous copies wait for each copy on a shared-memory
  * barrier; a wait that has not completed after one second of device time gives

@@ -37,7 +37,7 @@ EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option
            "dds_stress_noalloc",
            "dds_stress_host",
            "dds_table_at", "dds_query", "dds_launches_per_stress", "dds_profile_enable",
-           "dds_profile_read", "dds_device_status", "dds_last_error", "dds_destroy")
+           "dds_profile_read", "dds_relax", "dds_device_status", "dds_last_error", "dds_destroy")
 
 PASS_NAMES = ("x_fwd", "y_fwd", "z_fused", "y_inv", "x_inv")
 
@@ -79,6 +79,7 @@ def load_library():
         "dds_launches_per_stress": ([vp], ctypes.c_int),
         "dds_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
         "dds_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ip, ip], ctypes.c_int),
+        "dds_relax": ([vp, vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
         "dds_device_status": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "dds_last_error": ([vp], ctypes.c_char_p),
         "dds_destroy": ([vp], None),
@@ -173,6 +174,11 @@ def dds_stress_noalloc(ctx, rho_ptr: int, rho_dtype: int, sigma_ptr: int, stream
     """dds_stress with its work buffers in the library's fixed device area (no allocation)."""
     _check(ctx, load_library().dds_stress_noalloc(ctx, ctypes.c_void_p(rho_ptr), int(rho_dtype),
                                                   ctypes.c_void_p(sigma_ptr), _stream_handle(stream)))
+
+
+def dds_relax(ctx, sigma_dis_ptr: int, u_ptr: int, n_steps: int, sigma_tot_ptr: int = 0, stream=None):
+    _check(ctx, load_library().dds_relax(ctx, ctypes.c_void_p(sigma_dis_ptr), ctypes.c_void_p(u_ptr), int(n_steps),
+                                         ctypes.c_void_p(sigma_tot_ptr or None), _stream_handle(stream)))
 
 
 def dds_stress_host(ctx, rho_host: np.ndarray, sigma_host: np.ndarray, stream=None):
@@ -330,6 +336,25 @@ class StressContext:
             sigma_host = np.empty((6,) + self.shape, dtype=np.float32)
         dds_stress_host(self.handle, rho_host, sigma_host, stream)
         return sigma_host
+
+    def relax(self, sigma_dis, n_steps: int, u=None, total: bool = True, stream=None):
+        """Free-surface relaxation (Sec. 5) of sigma_dis (CUDA float32, (6, nz, ny, nx)).
+        u: CUDA float32 (3, nz, ny, nx) starting displacement, updated in place (default:
+        zeros).  Returns (u, sigma_tot) with sigma_tot None unless total."""
+        import torch
+        shape = self.shape
+        if not (sigma_dis.is_cuda and sigma_dis.dtype == torch.float32 and sigma_dis.is_contiguous()):
+            raise ValueError("sigma_dis must be a contiguous CUDA float32 tensor")
+        if sigma_dis.dim() != 4 or sigma_dis.shape[0] != 6 or (shape and tuple(sigma_dis.shape[1:]) != shape):
+            raise ValueError(f"sigma_dis has shape {tuple(sigma_dis.shape)}, expected (6,) + {shape}")
+        if u is None:
+            u = torch.zeros((3,) + tuple(sigma_dis.shape[1:]), dtype=torch.float32, device=sigma_dis.device)
+        elif not (u.is_cuda and u.dtype == torch.float32 and u.is_contiguous()
+                  and tuple(u.shape) == (3,) + tuple(sigma_dis.shape[1:])):
+            raise ValueError("u must be a contiguous CUDA float32 tensor of shape (3, nz, ny, nx)")
+        tot = torch.empty_like(sigma_dis) if total else None
+        dds_relax(self.handle, sigma_dis.data_ptr(), u.data_ptr(), n_steps, tot.data_ptr() if total else 0, stream)
+        return u, tot
 
     def table_at(self, t, b, ijk):
         return dds_table_at(self.handle, t, b, ijk)

@@ -554,6 +554,16 @@ int dds_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, void 
   return enqueue_stress(ctx, rho, rho_dtype, sigma, s);
 }
 
+int dds_relax(dds_ctx *ctx, const float *sigma_dis, float *u, int n_steps, float *sigma_tot, void *cuda_stream) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!ctx->has_geom) return fail(ctx, DDS_ERR_NOT_READY, "relax: call dds_set_geometry first");
+  if (ctx->nz < 2) return fail(ctx, DDS_ERR_UNSUPPORTED, "relax: the free surfaces need at least two layers");
+  if (!sigma_dis || !u) return fail(ctx, DDS_ERR_INVALID_ARG, "relax: NULL pointer");
+  if (n_steps < 0) return fail(ctx, DDS_ERR_INVALID_ARG, "relax: negative step count %d", n_steps);
+  DeviceGuard guard(ctx->device);
+  return enqueue_relax(ctx, sigma_dis, u, n_steps, sigma_tot, (cudaStream_t)cuda_stream);
+}
+
 int dds_stress_multi(dds_ctx *ctx, int nb, const void *rho, int rho_dtype, float *sigma, void *cuda_stream) {
   if (!ctx) return DDS_ERR_INVALID_ARG;
   if (!ctx->built) return fail(ctx, DDS_ERR_NOT_READY, "stress_multi: call dds_build_kernels first");
@@ -752,6 +762,7 @@ void dds_destroy(dds_ctx *ctx) {
     cudaFree(ctx->h2d_rho);
     cudaFree(ctx->h2d_sigma);
     cudaFree(ctx->stats);
+    cudaFree(ctx->relax_buf);
     for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
   }
   delete ctx;

@@ -92,6 +92,8 @@ struct dds_ctx {
   size_t bufA_n = 0, bufB_n = 0, nyqA_n = 0, nyqB_n = 0;
   int nb_cap = 1;                       // density sets the work buffers hold
   double *stats = nullptr;              // Eq. 20 sums, [set][6][nz]
+  float *relax_buf = nullptr;           // relaxation: dt f, u ping-pong, surface terms
+  size_t relax_n = 0;
   int stats_cap = 0;
   void *h2d_rho = nullptr;              // staging for dds_stress_host
   float *h2d_sigma = nullptr;
@@ -127,6 +129,9 @@ int build_spectra(dds_ctx *ctx, cudaStream_t s);
 int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s, int nb = 1,
                    double *stats = nullptr, float *s_out = nullptr);
 int stress_launch_count(const Shape &sh, const Collapse &col);
+
+// Free-surface relaxation (Sec. 5): n_steps explicit steps on u, then sigma_tot.
+int enqueue_relax(dds_ctx *ctx, const float *sig, float *u, int n_steps, float *sig_tot, cudaStream_t s);
 int enqueue_stress_buffers(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, float2 *bufA, float2 *bufB,
                            float2 *nyqA, float2 *nyqB, cudaStream_t s);
 

@@ -48,3 +48,26 @@ def test_gan_polycrystal_small():
     assert p.meta["n_grains"] == round((6.4e-6) ** 2 / (math.pi * 0.25e-12))
     p2 = W.gan_polycrystal(g, 1e-6, seed=3)
     assert np.array_equal(p.rho, p2.rho)
+
+
+def test_periodic_voronoi_is_nearest_periodic_image():
+    n, k, seed = 24, 10, 3
+    g = W.periodic_voronoi(n, k, seed)
+    u = W.uniform01(seed, np.arange(2 * k))
+    sx, sy = u[0::2], u[1::2]
+    for (j, i) in [(0, 0), (5, 23), (23, 11), (12, 12), (7, 0)]:
+        x, y = (i + 0.5) / n, (j + 0.5) / n
+        best = min(range(k), key=lambda s: (min(abs(x - sx[s]), 1 - abs(x - sx[s])) ** 2 +
+                                            min(abs(y - sy[s]), 1 - abs(y - sy[s])) ** 2, s))
+        assert g[j, i] == best
+
+
+def test_scaled_polycrystal_scales_one_pattern():
+    a = W.scaled_polycrystal(32, 4, 2e-6, 10e-6)
+    b = W.scaled_polycrystal(32, 4, 8e-6, 10e-6)
+    assert np.array_equal(a.rho, b.rho)
+    assert abs(b.geom.dx / a.geom.dx - 4.0) < 1e-12 and a.geom.dz == b.geom.dz
+    assert abs(a.geom.nx * a.geom.dx - 10 * 2e-6) < 1e-18
+    # every column carries exactly one orientation, uniform in height
+    assert np.all((a.rho > 0).sum(axis=0) == 1)
+    assert np.all(a.rho[:, 0] == a.rho[:, -1])

@@ -251,6 +251,50 @@ def gan_layer_256(seed: int = 0) -> Problem:
 SWEEP_GRIDS = [(128, 128, 64), (128, 128, 128), (256, 256, 64), (256, 256, 128)]
 
 
+def periodic_voronoi(n: int, n_seeds: int, seed: int) -> np.ndarray:
+    """Grain id per column (n, n) of a square cell grid with periodic sides: nearest of
+    ``n_seeds`` seeds drawn uniformly in the unit square, distances taken to the nearest
+    periodic image (ties to the lower id).  Scale-free: the same ids for every size."""
+    u = uniform01(seed, np.arange(2 * n_seeds))
+    sx, sy = u[0::2], u[1::2]
+    c = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    best = np.zeros(X.size, dtype=np.int64)
+    bestd = np.full(X.size, np.inf)
+    for k in range(n_seeds):                 # ascending ids; strict < keeps the lowest id on ties
+        dx = np.abs(X.ravel() - sx[k])
+        dy = np.abs(Y.ravel() - sy[k])
+        dx = np.minimum(dx, 1.0 - dx)
+        dy = np.minimum(dy, 1.0 - dy)
+        d = dx * dx + dy * dy
+        m = d < bestd
+        best[m] = k
+        bestd[m] = d[m]
+    return best.reshape(n, n)
+
+
+def scaled_polycrystal(n: int, nz: int, grain_size: float, thickness: float, n_grains: int = 100,
+                       seed: int = 0, rho_d: float = 1.0e9 * CM2) -> Problem:
+    """The grain-size study of Sec. 6.4-6.5: one fixed columnar grain pattern of
+    ``n_grains`` periodic Voronoi grains on a square of side L = 10 D (so the mean grain
+    area is D^2), scaled with D; vertical edge dislocations (t = z) whose Burgers vector
+    a_i is drawn per grain from the six in-plane orientations; density rho_d uniform in
+    height (the vertically homogeneous layer of Sec. 6.5).  n x n x nz cells over a
+    layer of the given thickness.  Six families, one per orientation."""
+    L = 10.0 * grain_size
+    geom = Geometry(n, n, nz, L / n, L / n, thickness / nz)
+    grains = periodic_voronoi(n, n_grains, seed)
+    u = uniform01(seed, 2 * n_grains + np.arange(n_grains))
+    orient = np.minimum((6.0 * u).astype(np.int64), 5)[grains]
+    t = np.array([T_Z] * 6)
+    b = np.array([hex_a(i) for i in range(6)])
+    rho = np.zeros((6, nz, n, n))
+    for f in range(6):
+        rho[f] = rho_d * (orient == f)[None, :, :]
+    return Problem(f"scaled_polycrystal_D{grain_size:.3g}_H{thickness:.3g}", geom, t, b, rho,
+                   meta={"n_grains": n_grains, "grain_size": grain_size, "thickness": thickness, "seed": seed})
+
+
 def sweep_realisation(r: int) -> Problem:
     """Realisation r of the grain-size sweep: grid drawn uniformly from SWEEP_GRIDS,
     cells 0.2x0.2x0.05 um, grain diameter log-uniform in [0.5, 8] um, grain seed r."""

@@ -110,35 +110,115 @@ __global__ void k_relax_prep(RelaxCoef r, const float *__restrict__ sig, float *
   }
 }
 
-// One explicit step: u_out = u_in + dt (navier(u_in) + f).
-__global__ void __launch_bounds__(128) k_relax_step(RelaxCoef r, const float *__restrict__ u, const float *__restrict__ gf,
-                                                    const float *__restrict__ phi, float *__restrict__ u_out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
-  if (i >= r.nx || j >= r.ny) return;
-  constexpr int d[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+// One explicit step, u_out = u_in + dt (navier(u_in) + f), on a tile of TX x TY columns
+// marching up a chunk of KZ layers: three planes (below, at, above the layer) of all
+// three components, with a one-cell halo, rotate through shared memory, so every value
+// of u is read from global memory about once per step (halo cells from L2).  The plane
+// two layers ahead is loaded into registers while the current layer is updated; ghost
+// planes are evaluated (uext) as they are loaded.
+constexpr int TX = 32, TY = 8, KZ = 16, HX = TX + 2, HY = TY + 2;
+constexpr int NT_TILE = TX * TY, PLANE = 3 * HY * HX, NQ = (PLANE + NT_TILE - 1) / NT_TILE;
+
+__device__ __forceinline__ int mod(int i, int n) { return ((i % n) + n) % n; }
+
+// The values of one plane (layer k, or a ghost layer) this thread stages: entry q of
+// the [component][y][x] halo tile for q = threadIdx.x + NT_TILE * e.
+__device__ __forceinline__ void fetch_plane(const RelaxCoef &r, const float *__restrict__ u,
+                                            const float *__restrict__ phi, const int (&col)[NQ], const int (&comp)[NQ],
+                                            int k, float (&v)[NQ]) {
+  const long plane = (long)r.ny * r.nx;
+  const bool film = k >= 0 && k < r.nz;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float c0 = uext(r, u, phi, a, i, j, k);
-    float v = __ldg(gf + cidx(r, a, k, j, i));
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const float up = uext(r, u, phi, a, i + d[b][0], j + d[b][1], k + d[b][2]);
-      const float um = uext(r, u, phi, a, i - d[b][0], j - d[b][1], k - d[b][2]);
-      v = fmaf(r.lap[a][b], (up - c0) + (um - c0), v);
+  for (int e = 0; e < NQ; ++e) {
+    if (comp[e] < 0) continue;
+    if (film) {
+      v[e] = __ldg(u + ((long)comp[e] * r.nz + k) * plane + col[e]);
+    } else {
+      const int j = col[e] / r.nx, i = col[e] - j * r.nx;
+      v[e] = uext(r, u, phi, comp[e], i, j, k);
     }
+  }
+}
+
+__device__ __forceinline__ void store_plane(const float (&v)[NQ], const int (&comp)[NQ], float *pl) {
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      if (b == a) continue;
-      // d^2 u_b / (da db), 4-point cross
-      const int sx = d[a][0] + d[b][0], sy = d[a][1] + d[b][1], sz = d[a][2] + d[b][2];
-      const int tx = d[a][0] - d[b][0], ty = d[a][1] - d[b][1], tz = d[a][2] - d[b][2];
-      const float pp = uext(r, u, phi, b, i + sx, j + sy, k + sz);
-      const float mm = uext(r, u, phi, b, i - sx, j - sy, k - sz);
-      const float pm = uext(r, u, phi, b, i + tx, j + ty, k + tz);
-      const float mp = uext(r, u, phi, b, i - tx, j - ty, k - tz);
-      v = fmaf(r.mix[a][b], (pp + mm) - (pm + mp), v);
+  for (int e = 0; e < NQ; ++e)
+    if (comp[e] >= 0) pl[threadIdx.x + NT_TILE * e] = v[e];
+}
+
+__global__ void __launch_bounds__(NT_TILE) k_relax_tile(RelaxCoef r, const float *__restrict__ u,
+                                                           const float *__restrict__ gf, const float *__restrict__ phi,
+                                                           float *__restrict__ u_out) {
+  __shared__ float pl[3][3][HY][HX];          // [slot][component][y][x]
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int kb = blockIdx.z * KZ, ke = min(kb + KZ, r.nz);
+  const int i = i0 + tx, j = j0 + ty;
+  const bool live = i < r.nx && j < r.ny;
+  // the halo entries this thread stages, fixed for the whole march: column j * nx + i
+  int col[NQ], comp[NQ];
+#pragma unroll
+  for (int e = 0; e < NQ; ++e) {
+    const int q = threadIdx.x + NT_TILE * e;
+    comp[e] = -1;
+    col[e] = 0;
+    if (q < PLANE) {
+      const int c = q / (HY * HX), rem = q - c * HY * HX;
+      const int hy = rem / HX, hx = rem - hy * HX;
+      comp[e] = c;
+      col[e] = mod(j0 + hy - 1, r.ny) * r.nx + mod(i0 + hx - 1, r.nx);
     }
-    u_out[cidx(r, a, k, j, i)] = c0 + v;
+  }
+  int sb = 0, sm = 1, sa = 2;                 // slots of the layers below, at, above
+  float v[NQ];
+  fetch_plane(r, u, phi, col, comp, kb - 1, v);
+  store_plane(v, comp, &pl[sb][0][0][0]);
+  fetch_plane(r, u, phi, col, comp, kb, v);
+  store_plane(v, comp, &pl[sm][0][0][0]);
+  fetch_plane(r, u, phi, col, comp, kb + 1, v);
+  store_plane(v, comp, &pl[sa][0][0][0]);
+  __syncthreads();
+  const int x = tx + 1, y = ty + 1;
+  for (int k = kb; k < ke; ++k) {
+    const bool more = k + 1 < ke;
+    if (more) fetch_plane(r, u, phi, col, comp, k + 2, v);     // in flight during this layer
+    if (live) {
+      float (*B)[HY][HX] = pl[sb];
+      float (*C)[HY][HX] = pl[sm];
+      float (*A)[HY][HX] = pl[sa];
+      float out[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float c0 = C[a][y][x];
+        float w = __ldg(gf + cidx(r, a, k, j, i));
+        w = fmaf(r.lap[a][0], (C[a][y][x + 1] - c0) + (C[a][y][x - 1] - c0), w);
+        w = fmaf(r.lap[a][1], (C[a][y + 1][x] - c0) + (C[a][y - 1][x] - c0), w);
+        w = fmaf(r.lap[a][2], (A[a][y][x] - c0) + (B[a][y][x] - c0), w);
+        out[a] = c0 + w;
+      }
+      // 4-point crosses: d2u_y/dxdy, d2u_z/dxdz into x; d2u_x/dxdy, d2u_z/dydz into y;
+      // d2u_x/dxdz, d2u_y/dydz into z
+      const float uy_xy = (C[1][y + 1][x + 1] + C[1][y - 1][x - 1]) - (C[1][y - 1][x + 1] + C[1][y + 1][x - 1]);
+      const float ux_xy = (C[0][y + 1][x + 1] + C[0][y - 1][x - 1]) - (C[0][y - 1][x + 1] + C[0][y + 1][x - 1]);
+      const float uz_xz = (A[2][y][x + 1] + B[2][y][x - 1]) - (B[2][y][x + 1] + A[2][y][x - 1]);
+      const float ux_xz = (A[0][y][x + 1] + B[0][y][x - 1]) - (B[0][y][x + 1] + A[0][y][x - 1]);
+      const float uz_yz = (A[2][y + 1][x] + B[2][y - 1][x]) - (B[2][y + 1][x] + A[2][y - 1][x]);
+      const float uy_yz = (A[1][y + 1][x] + B[1][y - 1][x]) - (B[1][y + 1][x] + A[1][y - 1][x]);
+      out[0] += r.mix[0][1] * uy_xy + r.mix[0][2] * uz_xz;
+      out[1] += r.mix[1][0] * ux_xy + r.mix[1][2] * uz_yz;
+      out[2] += r.mix[2][0] * ux_xz + r.mix[2][1] * uy_yz;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) u_out[cidx(r, a, k, j, i)] = out[a];
+    }
+    if (more) {
+      __syncthreads();                        // every thread is done with the plane below
+      const int t = sb;
+      sb = sm;
+      sm = sa;
+      sa = t;
+      store_plane(v, comp, &pl[sa][0][0][0]);
+      __syncthreads();
+    }
   }
 }
 
@@ -220,8 +300,9 @@ int enqueue_relax(dds_ctx *ctx, const float *sig, float *u, int n_steps, float *
     a = tmp;
     b = u;
   }
+  const dim3 tgrid((unsigned)((r.nx + TX - 1) / TX), (unsigned)((r.ny + TY - 1) / TY), (unsigned)((r.nz + KZ - 1) / KZ));
   for (int t = 0; t < n_steps && err == cudaSuccess; ++t) {
-    k_relax_step<<<grid, blk, 0, s>>>(r, a, gf, phi, b);
+    k_relax_tile<<<tgrid, NT_TILE, 0, s>>>(r, a, gf, phi, b);
     err = cudaGetLastError();
     std::swap(a, b);
   }

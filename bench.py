@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency measurement")
     ap.add_argument("--serving-seconds", type=float, default=5.0)
     ap.add_argument("--no-autotune", action="store_true", help="use the planner's default z schedule")
+    ap.add_argument("--no-relax", action="store_true", help="skip the free-surface relaxation measurement")
+    ap.add_argument("--no-grain", action="store_true", help="skip the grain-size scaling study")
     return ap.parse_args()
 
 
@@ -237,6 +239,72 @@ def cufft_comparator(p, q, steps: int = 20, warmup: int = 3):
 
 
 # ----------------------------------------------------------------- serving --
+def relaxation_benchmark(ctx, sigma, g, peak: float, steps: int = 200, cpu: bool = True):
+    """Free-surface relaxation (Sec. 5) of the evaluated stress on the same grid: device
+    time per explicit step (CUDA events around `steps` steps), the step's HBM roofline
+    (36 algorithmic bytes per cell: read u and dt f, write u), and the FP64 oracle's
+    time per step on the host for the same grid."""
+    import torch
+    import oracle.relax as R
+    u = torch.zeros((3, g.nz, g.ny, g.nx), dtype=torch.float32, device=sigma.device)
+    ctx.relax(sigma, 10, u=u, total=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.relax(sigma, steps, u=u, total=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    gbs = 36.0 * g.n_cells / (ms * 1e-3) / 1e9
+    out = {"steps": steps, "ms_per_step": ms, "cell_steps_per_s": g.n_cells / (ms * 1e-3),
+           "roofline": {"bound": "hbm", "bytes_per_cell_step": 36, "achieved": gbs, "peak": peak,
+                        "unit": "GB/s", "frac": gbs / peak},
+           "l2": "not flushed between steps (the 150 MB working set of a step exceeds L2)"}
+    if cpu:
+        sig = sigma.double().cpu().numpy()
+        h = (g.dx, g.dy, g.dz)
+        t = time.perf_counter()
+        R.relax(sig, h, g.mu, g.nu, 2)
+        dt = (time.perf_counter() - t) / 2
+        out["cpu_baseline"] = {"value": g.n_cells / dt, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                               "sample": f"2 explicit steps of the numpy FP64 relaxation on the full grid ({2 * dt:.1f} s)"}
+    return out
+
+
+def grain_scaling_study(device: int):
+    """Sec. 6.4-6.5: exponent of the in-plane stress deviation against the grain size D
+    for tall (H >> D, Eq. 27 predicts 1) and flat (H << D, Eq. 26 predicts 0) layers of
+    one scaled periodic grain pattern, with periodic boundary conditions (2 shells)."""
+    import numpy as np
+    import torch
+    import paper_1804_01830_gb300 as dds
+    um = 1e-6
+
+    def sdev(p, n_near):
+        gg = p.geom
+        c = dds.StressContext(device)
+        c.set_geometry(gg.nx, gg.ny, gg.nz, gg.dx, gg.dy, gg.dz, gg.mu, gg.nu).set_families(p.t, p.b)
+        c.set_option(dds.DDS_OPT_PBC_SHELLS, 2)
+        if n_near is not None:
+            c.set_option(dds.DDS_OPT_NEAR_RADIUS, n_near)
+        c.build_kernels()
+        sg = c.stress(torch.from_numpy(p.rho.astype(np.float32)).to(f"cuda:{device}"))
+        sd = sg.double().reshape(6, gg.nz, -1).std(dim=2).cpu().numpy()
+        c.close()
+        k0 = gg.nz // 4
+        return sd[:, k0:max(k0 + 1, 3 * gg.nz // 4)].mean(axis=1)
+
+    out = {}
+    for name, n, nz, H, Ds, nn, want in (("tall", 64, 8, 2000 * um, [1 * um, 2 * um, 4 * um], 0.0, 1.0),
+                                         ("flat", 64, 2, 0.2 * um, [10 * um, 20 * um, 40 * um], None, 0.0)):
+        sd = np.array([sdev(W.scaled_polycrystal(n, nz, D, H), nn) for D in Ds])
+        ex = {c: float(np.polyfit(np.log(Ds), np.log(sd[:, i]), 1)[0])
+              for i, c in ((0, "xx"), (1, "yy"), (3, "xy"), (2, "zz"))}
+        out[name] = {"grid": [n, n, nz], "thickness_um": H / um, "grain_sizes_um": [D / um for D in Ds],
+                     "exponents": ex, "predicted": want}
+    return out
+
+
 def serving_benchmark(device: int, duration: float, rate: float = 200.0, budget: float = 150e9, seed: int = 0):
     """Poisson stream of stress requests (mixed grids, cell aspects and family sets)
     through the continuous-batching server; kernel spectra cached per geometry (warmed
@@ -465,6 +533,14 @@ def run_ours(args):
                    "stated_bound_vs_fp64": 5e-4}
         ctx16.close()
 
+    relaxation = None
+    if not args.no_relax and rank == 0 and world == 1 and g.nz >= 2:
+        relaxation = relaxation_benchmark(ctx, sigma, g, peak, cpu=not args.no_cpu_baseline)
+
+    grain = None
+    if not args.no_grain and rank == 0 and world == 1:
+        grain = grain_scaling_study(local)
+
     serving = None
     if not args.no_serving and rank == 0 and world == 1:
         serving = serving_benchmark(local, args.serving_seconds)
@@ -501,6 +577,8 @@ def run_ours(args):
         "gpu_comparator": comparator,
         "reduced_storage": reduced,
         "serving": serving,
+        "relaxation": relaxation,
+        "grain_size_scaling": grain,
         "cpu_baseline": cpu,
         "gpu_launches": K * ctx.launches_per_stress,
         "clocks": clk,

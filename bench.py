@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="use the planner's default z schedule")
     ap.add_argument("--no-relax", action="store_true", help="skip the free-surface relaxation measurement")
     ap.add_argument("--no-grain", action="store_true", help="skip the grain-size scaling study")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 64-realisation batched sweep")
     return ap.parse_args()
 
 
@@ -305,6 +306,99 @@ def grain_scaling_study(device: int):
     return out
 
 
+def sweep_benchmark(device: int, n_real: int = 64, reps: int = 5, oracle_targets: int = 6):
+    """The batched grain-size sweep: n_real polycrystal realisations on the four sweep
+    grids (cells 0.2x0.2x0.05 um, 18 families, grain diameters log-uniform in 0.5-8 um),
+    one context per grid with an autotuned z schedule, all realisations of a grid in one
+    batch, and the whole sweep captured as one CUDA graph (FP32 densities, and again with
+    BF16 densities).  Time per sweep over `reps` graph launches (CUDA events); the same
+    realisations evaluated one by one for comparison; BF16 against FP32; one realisation
+    against the FP64 oracle on sampled target cells."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_1804_01830_gb300 as dds
+    dev = f"cuda:{device}"
+    groups = {}
+    for r in range(n_real):
+        g, D = W.sweep_spec(r)
+        groups.setdefault((g.nx, g.ny, g.nz), []).append((r, g, D))
+    ctxs, rho32, rho16, cells = [], [], [], 0
+    t_build = time.perf_counter()
+    for key, items in sorted(groups.items()):
+        g = items[0][1]
+        t, b = W.gan_families()
+        ctx = dds.StressContext(device)
+        ctx.set_geometry(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.mu, g.nu).set_families(t, b)
+        ctx.autotune()
+        ctx.build_kernels()
+        rho = torch.empty((len(items), t.shape[0], g.nz, g.ny, g.nx), dtype=torch.float32, device=dev)
+        for i, (r, gg, D) in enumerate(items):
+            _, _, mask, prof, _ = W.gan_polycrystal_parts(gg, D, r)
+            m = torch.from_numpy(mask).to(dev, torch.float32)
+            pz = torch.from_numpy(prof.astype(np.float32)).to(dev)
+            rho[i] = pz[None, :, None, None] * m[:, None, :, :]
+        ctxs.append(ctx)
+        rho32.append(rho)
+        rho16.append(rho.to(torch.bfloat16))
+        cells += len(items) * g.n_cells
+    torch.cuda.synchronize(device)
+    t_build = time.perf_counter() - t_build
+    g32 = dds.StressGraph(list(zip(ctxs, rho32)))
+    g16 = dds.StressGraph(list(zip(ctxs, rho16)))
+    out = {"realisations": n_real, "grids": {f"{k[0]}x{k[1]}x{k[2]}": len(v) for k, v in sorted(groups.items())},
+           "cells_per_sweep": cells, "families": 18, "graph_nodes": g32.nodes,
+           "setup_s (tables, spectra, autotune, densities)": t_build,
+           "l2": "not flushed: every sweep streams > 100 GB, far beyond L2"}
+    for name, gr in (("fp32", g32), ("bf16_densities", g16)):
+        gr.launch()
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            gr.launch()
+        e1.record()
+        torch.cuda.synchronize(device)
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_sweep": ms, "cells_per_s": cells / (ms * 1e-3),
+                     "realisations_per_s": n_real / (ms * 1e-3)}
+    # one by one, no batching and no graph
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for ctx, rho in zip(ctxs, rho32):
+        for i in range(rho.shape[0]):
+            ctx.stress(rho[i])
+    e1.record()
+    torch.cuda.synchronize(device)
+    out["one_by_one_ms"] = e0.elapsed_time(e1)
+    d = max(float(((a.double() - b.double()).reshape(a.shape[0], 6, -1).norm(dim=2) /
+                   b.double().reshape(b.shape[0], 6, -1).norm(dim=2).clamp_min(1e-30)).max())
+            for a, b in zip(g16.sigma, g32.sigma))
+    out["bf16_rel_l2_vs_fp32_max"] = d
+    # realisation 0 against the FP64 oracle on sampled targets
+    r0 = 0
+    g0, D0 = W.sweep_spec(r0)
+    k0 = sorted(groups).index((g0.nx, g0.ny, g0.nz))
+    i0 = [r for r, _, _ in groups[(g0.nx, g0.ny, g0.nz)]].index(r0)
+    p0 = W.gan_polycrystal(g0, D0, r0)
+    tg = np.random.default_rng(0).integers(0, g0.n_cells, size=oracle_targets)
+    t_or = time.perf_counter()
+    ref = oracle.stress_direct(g0, p0.t, p0.b, p0.rho, targets=tg, use_table=False).T
+    t_or = time.perf_counter() - t_or
+    got = g32.sigma[k0][i0].reshape(6, -1)[:, torch.from_numpy(tg).to(dev)].double().cpu().numpy()
+    scale = max(np.linalg.norm(ref[c]) for c in range(6))
+    rel = max(np.linalg.norm(got[c] - ref[c]) / max(np.linalg.norm(ref[c]), 1e-6 * scale) for c in range(6))
+    out["oracle_check"] = {"realisation": r0, "targets": int(tg.size), "rel_l2_max": float(rel),
+                           "oracle_s": t_or}
+    g32.close()
+    g16.close()
+    for c in ctxs:
+        c.close()
+    del rho32, rho16
+    torch.cuda.empty_cache()
+    return out
+
+
 def serving_benchmark(device: int, duration: float, rate: float = 200.0, budget: float = 150e9, seed: int = 0):
     """Poisson stream of stress requests (mixed grids, cell aspects and family sets)
     through the continuous-batching server; kernel spectra cached per geometry (warmed
@@ -541,6 +635,10 @@ def run_ours(args):
     if not args.no_grain and rank == 0 and world == 1:
         grain = grain_scaling_study(local)
 
+    sweep = None
+    if not args.no_sweep and rank == 0 and world == 1:
+        sweep = sweep_benchmark(local)
+
     serving = None
     if not args.no_serving and rank == 0 and world == 1:
         serving = serving_benchmark(local, args.serving_seconds)
@@ -579,6 +677,7 @@ def run_ours(args):
         "serving": serving,
         "relaxation": relaxation,
         "grain_size_scaling": grain,
+        "batched_sweep": sweep,
         "cpu_baseline": cpu,
         "gpu_launches": K * ctx.launches_per_stress,
         "clocks": clk,

@@ -155,6 +155,27 @@ int dds_stress_stats(dds_ctx *ctx, int nb, const void *rho, int rho_dtype, float
 int dds_stress_batched(dds_ctx **ctxs, int n, const void **rho, const int *rho_dtype,
                        float **sigma, void *cuda_stream);
 
+/* Captured batches (CUDA graphs).  Many density sets on many grids become one
+ * graph launch: dds_graph_capture records, for every entry i, the passes of
+ * dds_stress_multi(ctxs[i], nb[i], rho[i], rho_dtype[i], sigma[i]) into one CUDA
+ * graph; dds_graph_launch replays them all with a single launch call on any stream.
+ * The graph holds the device pointers it was captured with: refill rho[i] in place
+ * between launches and read sigma[i] after.  Capture first sizes each context's
+ * work buffers for its batch (may synchronise the device) and runs every entry once
+ * on `cuda_stream` (this writes sigma and completes the library's one-time set-up),
+ * then records on a private stream.  Contexts must be built, on one device, with
+ * per-pass profiling off; while a graph exists, do not change or destroy its
+ * contexts, and do not run other evaluations on them concurrently with a launch
+ * (they share the work buffers).  rho_dtype may be NULL (all DDS_F32).  The batch
+ * sweep of Sec. 6.4-style realisations is the intended use. */
+typedef struct dds_graph dds_graph;
+int dds_graph_capture(dds_ctx **ctxs, int n, const int *nb, const void **rho, const int *rho_dtype, float **sigma,
+                      void *cuda_stream, dds_graph **out);
+int dds_graph_launch(dds_graph *graph, void *cuda_stream);
+/* Number of nodes (kernels and memsets) in the captured graph. */
+int dds_graph_nodes(const dds_graph *graph);
+void dds_graph_destroy(dds_graph *graph);
+
 /* Size of the fixed device work area used by dds_stress_noalloc (32 MiB). */
 #define DDS_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -37,7 +37,8 @@ EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option
            "dds_stress_noalloc",
            "dds_stress_host",
            "dds_table_at", "dds_query", "dds_launches_per_stress", "dds_profile_enable",
-           "dds_profile_read", "dds_relax", "dds_device_status", "dds_last_error", "dds_destroy")
+           "dds_profile_read", "dds_relax", "dds_graph_capture", "dds_graph_launch", "dds_graph_nodes",
+           "dds_graph_destroy", "dds_device_status", "dds_last_error", "dds_destroy")
 
 PASS_NAMES = ("x_fwd", "y_fwd", "z_fused", "y_inv", "x_inv")
 
@@ -80,6 +81,11 @@ def load_library():
         "dds_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
         "dds_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ip, ip], ctypes.c_int),
         "dds_relax": ([vp, vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "dds_graph_capture": ([ctypes.POINTER(vp), ctypes.c_int, ip, ctypes.POINTER(vp), ip, ctypes.POINTER(vp), vp,
+                               ctypes.POINTER(vp)], ctypes.c_int),
+        "dds_graph_launch": ([vp, vp], ctypes.c_int),
+        "dds_graph_nodes": ([vp], ctypes.c_int),
+        "dds_graph_destroy": ([vp], None),
         "dds_device_status": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "dds_last_error": ([vp], ctypes.c_char_p),
         "dds_destroy": ([vp], None),
@@ -221,6 +227,81 @@ def dds_profile_read(ctx, max_steps: int) -> np.ndarray:
                                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                                 ctypes.byref(ns), ctypes.byref(npass)))
     return out[: ns.value, : npass.value]
+
+
+def dds_graph_capture(ctxs, nbs, rho_ptrs, dtypes, sigma_ptrs, stream=None) -> ctypes.c_void_p:
+    """Capture the batch; returns the graph handle (raises DDSError)."""
+    n = len(ctxs)
+    h = ctypes.c_void_p()
+    rc = load_library().dds_graph_capture((ctypes.c_void_p * n)(*ctxs), n, (ctypes.c_int * n)(*nbs),
+                                          (ctypes.c_void_p * n)(*rho_ptrs), (ctypes.c_int * n)(*dtypes),
+                                          (ctypes.c_void_p * n)(*sigma_ptrs), _stream_handle(stream),
+                                          ctypes.byref(h))
+    if rc != DDS_OK:
+        raise DDSError(rc, dds_last_error(ctxs[0]) if n else "")
+    return h
+
+
+def dds_graph_launch(graph, stream=None):
+    rc = load_library().dds_graph_launch(graph, _stream_handle(stream))
+    if rc != DDS_OK:
+        raise DDSError(rc, "graph launch failed")
+
+
+def dds_graph_nodes(graph) -> int:
+    return int(load_library().dds_graph_nodes(graph))
+
+
+def dds_graph_destroy(graph):
+    if graph:
+        load_library().dds_graph_destroy(graph)
+
+
+class StressGraph:
+    """A captured batch: entries (context, densities) -> sigma replayed by one launch.
+
+    entries: list of (StressContext, rho) with rho a contiguous CUDA tensor of shape
+    (nb, F, nz, ny, nx) (float32 or bfloat16); the outputs (nb, 6, nz, ny, nx) are
+    allocated here and exposed as ``sigma``.  Refill the rho tensors in place between
+    launches."""
+
+    def __init__(self, entries, stream=None):
+        import torch
+        self.entries = entries
+        self.sigma = []
+        ctxs, nbs, rhos, dts, sigs = [], [], [], [], []
+        for ctx, rho in entries:
+            if rho.dim() != 5 or not rho.is_cuda or not rho.is_contiguous():
+                raise ValueError("rho must be a contiguous 5-d CUDA tensor (nb, F, nz, ny, nx)")
+            dt = {torch.float32: DDS_F32, torch.bfloat16: DDS_BF16}.get(rho.dtype)
+            if dt is None:
+                raise ValueError(f"unsupported density dtype {rho.dtype}")
+            sig = torch.empty((rho.shape[0], 6) + tuple(rho.shape[2:]), dtype=torch.float32, device=rho.device)
+            self.sigma.append(sig)
+            ctxs.append(ctx.handle)
+            nbs.append(int(rho.shape[0]))
+            rhos.append(rho.data_ptr())
+            dts.append(dt)
+            sigs.append(sig.data_ptr())
+        self._handle = dds_graph_capture(ctxs, nbs, rhos, dts, sigs, stream)
+
+    @property
+    def nodes(self) -> int:
+        return dds_graph_nodes(self._handle)
+
+    def launch(self, stream=None):
+        dds_graph_launch(self._handle, stream)
+
+    def close(self):
+        if self._handle:
+            dds_graph_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def dds_device_status(device: int = 0, reset: bool = False) -> int:

@@ -639,6 +639,112 @@ int dds_stress_batched(dds_ctx **ctxs, int n, const void **rho, const int *rho_d
   return DDS_OK;
 }
 
+struct dds_graph {
+  int device = 0;
+  int n = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+int dds_graph_capture(dds_ctx **ctxs, int n, const int *nb, const void **rho, const int *rho_dtype, float **sigma,
+                      void *cuda_stream, dds_graph **out) {
+  if (!out) return DDS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!ctxs || n < 1 || !nb || !rho || !sigma) return DDS_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    dds_ctx *c = ctxs[i];
+    if (!c) return DDS_ERR_INVALID_ARG;
+    if (c->device != ctxs[0]->device) return fail(c, DDS_ERR_INVALID_ARG, "graph_capture: contexts on different devices");
+    if (!c->built) return fail(c, DDS_ERR_NOT_READY, "graph_capture: call dds_build_kernels first");
+    if (c->profiling) return fail(c, DDS_ERR_INVALID_ARG, "graph_capture: disable per-pass profiling first");
+    if (nb[i] < 1 || nb[i] > 4096) return fail(c, DDS_ERR_INVALID_ARG, "graph_capture: nb = %d outside [1, 4096]", nb[i]);
+    const int dt = rho_dtype ? rho_dtype[i] : DDS_F32;
+    if (dt != DDS_F32 && dt != DDS_BF16) return fail(c, DDS_ERR_INVALID_ARG, "graph_capture: unknown density type %d", dt);
+    if (!rho[i] || !sigma[i] || ((uintptr_t)rho[i] & 15) || ((uintptr_t)sigma[i] & 15))
+      return fail(c, DDS_ERR_INVALID_ARG, "graph_capture: rho and sigma must be non-NULL and 16-byte aligned");
+  }
+  DeviceGuard guard(ctxs[0]->device);
+  cudaStream_t user = (cudaStream_t)cuda_stream;
+  // work buffers for every batch, then one evaluation of each entry outside the capture
+  // (finishes the library's lazy per-device set-up; writes sigma)
+  for (int i = 0; i < n; ++i) {
+    if (nb[i] > ctxs[i]->nb_cap) {
+      const cudaError_t err = cudaDeviceSynchronize();
+      if (err != cudaSuccess) return fail(ctxs[i], DDS_ERR_CUDA, "graph_capture: %s", cudaGetErrorString(err));
+      const int rc = alloc_work(ctxs[i], nb[i]);
+      if (rc != DDS_OK) return rc;
+    }
+    if (ctxs[i]->fe == 0) continue;
+    const int rc = enqueue_stress(ctxs[i], rho[i], rho_dtype ? rho_dtype[i] : DDS_F32, sigma[i], user, nb[i]);
+    if (rc != DDS_OK) return rc;
+  }
+  cudaError_t err = cudaStreamSynchronize(user);
+  if (err != cudaSuccess) return fail(ctxs[0], DDS_ERR_CUDA, "graph_capture: %s", cudaGetErrorString(err));
+  cudaStream_t cs = nullptr;
+  err = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (err != cudaSuccess) return fail(ctxs[0], DDS_ERR_CUDA, "graph_capture: %s", cudaGetErrorString(err));
+  err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  int rc = DDS_OK;
+  for (int i = 0; i < n && err == cudaSuccess && rc == DDS_OK; ++i) {
+    if (ctxs[i]->fe == 0) {
+      err = cudaMemsetAsync(sigma[i], 0, sizeof(float) * 6 * (size_t)nb[i] * ctxs[i]->nx * ctxs[i]->ny * ctxs[i]->nz, cs);
+      continue;
+    }
+    rc = enqueue_stress(ctxs[i], rho[i], rho_dtype ? rho_dtype[i] : DDS_F32, sigma[i], cs, nb[i]);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t end = cudaStreamEndCapture(cs, &graph);
+  cudaStreamDestroy(cs);
+  if (err == cudaSuccess) err = end;
+  cudaGraphExec_t exec = nullptr;
+  if (err == cudaSuccess && rc == DDS_OK) err = cudaGraphInstantiate(&exec, graph, 0);
+  if (err != cudaSuccess || rc != DDS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc != DDS_OK ? rc : fail(ctxs[0], DDS_ERR_CUDA, "graph_capture: %s", cudaGetErrorString(err));
+  }
+  dds_graph *g = new (std::nothrow) dds_graph;
+  if (!g) {
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    return DDS_ERR_OOM;
+  }
+  g->device = ctxs[0]->device;
+  g->n = n;
+  g->graph = graph;
+  g->exec = exec;
+  *out = g;
+  return DDS_OK;
+}
+
+int dds_graph_launch(dds_graph *g, void *cuda_stream) {
+  if (!g) return DDS_ERR_INVALID_ARG;
+  DeviceGuard guard(g->device);
+  const cudaError_t err = cudaGraphLaunch(g->exec, (cudaStream_t)cuda_stream);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return DDS_ERR_CUDA;
+  }
+  return DDS_OK;
+}
+
+int dds_graph_nodes(const dds_graph *g) {
+  if (!g) return DDS_ERR_INVALID_ARG;
+  size_t nodes = 0;
+  if (cudaGraphGetNodes(g->graph, nullptr, &nodes) != cudaSuccess) return DDS_ERR_CUDA;
+  return (int)nodes;
+}
+
+void dds_graph_destroy(dds_graph *g) {
+  if (!g) return;
+  {
+    DeviceGuard guard(g->device);
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+  }
+  delete g;
+}
+
 int dds_stress_host(dds_ctx *ctx, const float *rho_host, float *sigma_host, void *cuda_stream) {
   if (!ctx) return DDS_ERR_INVALID_ARG;
   if (!ctx->built) return fail(ctx, DDS_ERR_NOT_READY, "stress_host: call dds_build_kernels first");

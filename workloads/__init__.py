@@ -215,11 +215,10 @@ def gan_height_profile(geom: Geometry) -> np.ndarray:
     return (1.0e10 * np.exp(-z / (0.5 * UM)) + 1.0e8) * CM2
 
 
-def gan_polycrystal(geom: Geometry, grain_diameter: float, seed: int,
-                    name: str = "gan_polycrystal") -> Problem:
-    """Columnar Voronoi polycrystal with mean grain diameter ``grain_diameter``.
-    Each grain draws one edge family (b = a_i) and one mixed family (b = a_i +- c);
-    both carry the height profile rho(z) in every cell of the grain."""
+def gan_polycrystal_parts(geom: Geometry, grain_diameter: float, seed: int):
+    """The factors of ``gan_polycrystal``'s density: per family a column mask (F, ny, nx)
+    and the height profile rho(z) (nz,), so that rho[f, z, y, x] = prof[z] * mask[f, y, x].
+    Returns (t, b, mask, prof, n_grains)."""
     Lx, Ly = geom.nx * geom.dx, geom.ny * geom.dy
     n_seeds = max(1, int(round(Lx * Ly / (math.pi * (grain_diameter / 2.0) ** 2))))
     grains = voronoi_columns(geom, n_seeds, seed)
@@ -229,16 +228,22 @@ def gan_polycrystal(geom: Geometry, grain_diameter: float, seed: int,
     mix_sign = (u[2::3] >= 0.5).astype(np.int64)         # 0 -> +c, 1 -> -c
     t, b = gan_families()
     F = t.shape[0]
-    prof = gan_height_profile(geom)
-    rho = np.zeros((F, geom.nz, geom.ny, geom.nx), dtype=np.float64)
     fam_edge = edge_idx[grains]                          # (ny, nx)
     fam_mix = 6 + 2 * mix_idx[grains] + mix_sign[grains]
-    for f in range(F):
-        mask = (fam_edge == f) | (fam_mix == f)
-        if mask.any():
-            rho[f] = prof[:, None, None] * mask[None, :, :]
+    mask = np.stack([(fam_edge == f) | (fam_mix == f) for f in range(F)])
+    return t, b, mask, gan_height_profile(geom), n_seeds
+
+
+def gan_polycrystal(geom: Geometry, grain_diameter: float, seed: int,
+                    name: str = "gan_polycrystal") -> Problem:
+    """Columnar Voronoi polycrystal with mean grain diameter ``grain_diameter``.
+    Each grain draws one edge family (b = a_i) and one mixed family (b = a_i +- c);
+    both carry the height profile rho(z) in every cell of the grain."""
+    t, b, mask, prof, n_seeds = gan_polycrystal_parts(geom, grain_diameter, seed)
+    rho = prof[None, :, None, None] * mask[:, None, :, :].astype(np.float64)
     return Problem(name, geom, t, b, rho,
                    meta={"n_grains": n_seeds, "grain_diameter": grain_diameter, "seed": seed})
+
 
 
 def gan_layer_256(seed: int = 0) -> Problem:
@@ -295,13 +300,19 @@ def scaled_polycrystal(n: int, nz: int, grain_size: float, thickness: float, n_g
                    meta={"n_grains": n_grains, "grain_size": grain_size, "thickness": thickness, "seed": seed})
 
 
-def sweep_realisation(r: int) -> Problem:
-    """Realisation r of the grain-size sweep: grid drawn uniformly from SWEEP_GRIDS,
-    cells 0.2x0.2x0.05 um, grain diameter log-uniform in [0.5, 8] um, grain seed r."""
+def sweep_spec(r: int):
+    """Grid and grain diameter of realisation r of the grain-size sweep: grid drawn
+    uniformly from SWEEP_GRIDS, grain diameter log-uniform in [0.5, 8] um."""
     u = uniform01(1000 + r, np.arange(2))
     nx, ny, nz = SWEEP_GRIDS[min(int(4 * u[0]), 3)]
     D = math.exp(math.log(0.5) + (math.log(8.0) - math.log(0.5)) * u[1]) * UM
-    g = Geometry(nx, ny, nz, 0.2 * UM, 0.2 * UM, 0.05 * UM)
+    return Geometry(nx, ny, nz, 0.2 * UM, 0.2 * UM, 0.05 * UM), D
+
+
+def sweep_realisation(r: int) -> Problem:
+    """Realisation r of the grain-size sweep: cells 0.2x0.2x0.05 um, grid and grain
+    diameter from sweep_spec(r), grain seed r."""
+    g, D = sweep_spec(r)
     return gan_polycrystal(g, D, r, name=f"sweep_{r}")
 
 

@@ -336,7 +336,7 @@ __device__ __forceinline__ float2 load_pair(const void *rho, long o, int n2x, in
   if (BF16) {
     const uint16_t *r = (const uint16_t *)rho;
     if (even) {                                 // both values in one aligned 32-bit word
-      const uint32_t w = __ldcs(reinterpret_cast<const unsigned int *>(r + o));
+      const uint32_t w = __ldg(reinterpret_cast<const unsigned int *>(r + o));
       return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
     }
     return make_float2(bf16_to_f32(r[o]), n2x + 1 < nx ? bf16_to_f32(r[o + 1]) : 0.f);

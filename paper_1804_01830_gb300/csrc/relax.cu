@@ -122,19 +122,23 @@ constexpr int NT_TILE = TX * TY, PLANE = 3 * HY * HX, NQ = (PLANE + NT_TILE - 1)
 __device__ __forceinline__ int mod(int i, int n) { return ((i % n) + n) % n; }
 
 // The values of one plane (layer k, or a ghost layer) this thread stages: entry q of
-// the [component][y][x] halo tile for q = threadIdx.x + NT_TILE * e.
+// the [component][y][x] halo tile for q = threadIdx.x + NT_TILE * e, whose film
+// element is u[base[e] + k * plane] (32-bit offsets: 3 nx ny nz < 2^31 for every grid
+// the library accepts).
 __device__ __forceinline__ void fetch_plane(const RelaxCoef &r, const float *__restrict__ u,
-                                            const float *__restrict__ phi, const int (&col)[NQ], const int (&comp)[NQ],
-                                            int k, float (&v)[NQ]) {
-  const long plane = (long)r.ny * r.nx;
-  const bool film = k >= 0 && k < r.nz;
+                                            const float *__restrict__ phi, const int (&base)[NQ], const int (&comp)[NQ],
+                                            int k, int plane, float (&v)[NQ]) {
+  if (k >= 0 && k < r.nz) {
+    const int kp = k * plane;
 #pragma unroll
-  for (int e = 0; e < NQ; ++e) {
-    if (comp[e] < 0) continue;
-    if (film) {
-      v[e] = __ldg(u + ((long)comp[e] * r.nz + k) * plane + col[e]);
-    } else {
-      const int j = col[e] / r.nx, i = col[e] - j * r.nx;
+    for (int e = 0; e < NQ; ++e)
+      if (comp[e] >= 0) v[e] = __ldg(u + base[e] + kp);
+  } else {
+#pragma unroll
+    for (int e = 0; e < NQ; ++e) {
+      if (comp[e] < 0) continue;
+      const int col = base[e] - comp[e] * r.nz * plane;
+      const int j = col / r.nx, i = col - j * r.nx;
       v[e] = uext(r, u, phi, comp[e], i, j, k);
     }
   }
@@ -147,50 +151,53 @@ __device__ __forceinline__ void store_plane(const float (&v)[NQ], const int (&co
 }
 
 __global__ void __launch_bounds__(NT_TILE) k_relax_tile(RelaxCoef r, const float *__restrict__ u,
-                                                           const float *__restrict__ gf, const float *__restrict__ phi,
-                                                           float *__restrict__ u_out) {
+                                                        const float *__restrict__ gf, const float *__restrict__ phi,
+                                                        float *__restrict__ u_out) {
   __shared__ float pl[3][3][HY][HX];          // [slot][component][y][x]
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int kb = blockIdx.z * KZ, ke = min(kb + KZ, r.nz);
   const int i = i0 + tx, j = j0 + ty;
   const bool live = i < r.nx && j < r.ny;
-  // the halo entries this thread stages, fixed for the whole march: column j * nx + i
-  int col[NQ], comp[NQ];
+  const int plane = r.ny * r.nx, cstride = r.nz * plane;
+  const int own = j * r.nx + i;
+  // the halo entries this thread stages, fixed for the whole march
+  int base[NQ], comp[NQ];
 #pragma unroll
   for (int e = 0; e < NQ; ++e) {
     const int q = threadIdx.x + NT_TILE * e;
     comp[e] = -1;
-    col[e] = 0;
+    base[e] = 0;
     if (q < PLANE) {
       const int c = q / (HY * HX), rem = q - c * HY * HX;
       const int hy = rem / HX, hx = rem - hy * HX;
       comp[e] = c;
-      col[e] = mod(j0 + hy - 1, r.ny) * r.nx + mod(i0 + hx - 1, r.nx);
+      base[e] = c * cstride + mod(j0 + hy - 1, r.ny) * r.nx + mod(i0 + hx - 1, r.nx);
     }
   }
   int sb = 0, sm = 1, sa = 2;                 // slots of the layers below, at, above
   float v[NQ];
-  fetch_plane(r, u, phi, col, comp, kb - 1, v);
+  fetch_plane(r, u, phi, base, comp, kb - 1, plane, v);
   store_plane(v, comp, &pl[sb][0][0][0]);
-  fetch_plane(r, u, phi, col, comp, kb, v);
+  fetch_plane(r, u, phi, base, comp, kb, plane, v);
   store_plane(v, comp, &pl[sm][0][0][0]);
-  fetch_plane(r, u, phi, col, comp, kb + 1, v);
+  fetch_plane(r, u, phi, base, comp, kb + 1, plane, v);
   store_plane(v, comp, &pl[sa][0][0][0]);
   __syncthreads();
   const int x = tx + 1, y = ty + 1;
   for (int k = kb; k < ke; ++k) {
     const bool more = k + 1 < ke;
-    if (more) fetch_plane(r, u, phi, col, comp, k + 2, v);     // in flight during this layer
+    if (more) fetch_plane(r, u, phi, base, comp, k + 2, plane, v);     // in flight during this layer
     if (live) {
       float (*B)[HY][HX] = pl[sb];
       float (*C)[HY][HX] = pl[sm];
       float (*A)[HY][HX] = pl[sa];
+      const int o = k * plane + own;
       float out[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const float c0 = C[a][y][x];
-        float w = __ldg(gf + cidx(r, a, k, j, i));
+        float w = __ldg(gf + a * cstride + o);
         w = fmaf(r.lap[a][0], (C[a][y][x + 1] - c0) + (C[a][y][x - 1] - c0), w);
         w = fmaf(r.lap[a][1], (C[a][y + 1][x] - c0) + (C[a][y - 1][x] - c0), w);
         w = fmaf(r.lap[a][2], (A[a][y][x] - c0) + (B[a][y][x] - c0), w);
@@ -208,7 +215,7 @@ __global__ void __launch_bounds__(NT_TILE) k_relax_tile(RelaxCoef r, const float
       out[1] += r.mix[1][0] * ux_xy + r.mix[1][2] * uz_yz;
       out[2] += r.mix[2][0] * ux_xz + r.mix[2][1] * uy_yz;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) u_out[cidx(r, a, k, j, i)] = out[a];
+      for (int a = 0; a < 3; ++a) u_out[a * cstride + o] = out[a];
     }
     if (more) {
       __syncthreads();                        // every thread is done with the plane below

@@ -113,3 +113,22 @@ def test_shell_option_validation(dds):
             ctx.set_option(dds.DDS_OPT_PBC_SHELLS, bad)
     ctx.set_option(dds.DDS_OPT_PBC_SHELLS, 0)
     ctx.close()
+
+
+def test_replica_table_sampled_at_full_size(dds):
+    # the GaN layer's geometry with two replica shells, sampled offsets (far, near, corners)
+    g = W.Geometry(256, 256, 128, 0.2e-6, 0.2e-6, 0.05e-6)
+    ctx = dds.StressContext(0)
+    ctx.set_geometry(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.mu, g.nu)
+    ctx.set_option(dds.DDS_OPT_PBC_SHELLS, 2)
+    rng = np.random.default_rng(5)
+    ijk = np.concatenate([rng.integers(-255, 256, size=(40, 2)), rng.integers(-127, 128, size=(40, 1))], axis=1)
+    ijk = np.concatenate([ijk, rng.integers(-3, 4, size=(20, 3)),
+                          np.array([[255, 255, 127], [-255, 0, 0], [0, 0, 0], [0, -255, 1]])])
+    t_all, b_all = W.gan_families()
+    for f in (4, 13):
+        got = ctx.table_at(t_all[f], b_all[f], ijk)
+        ref = np.array([oracle.interaction_pbc(g, *o, t_all[f], b_all[f], 2) for o in ijk])
+        for c in range(6):
+            assert np.abs(got[:, c] - ref[:, c]).max() <= TOL_TABLE * np.abs(ref[:, c]).max(), (f, c)
+    ctx.close()

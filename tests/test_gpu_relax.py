@@ -208,3 +208,24 @@ def test_relax_error_codes(dds):
         ctx.relax(torch.zeros((6, 2, 4, 4), device="cuda"), -1)
     assert e.value.code == dds.DDS_ERR_INVALID_ARG
     ctx.close()
+
+
+@pytest.mark.parametrize("workload", ["radial_disk_512x512x16", "gan_layer_256x256x128"])
+def test_full_size_steps_match_oracle(dds, workload):
+    # the bench grids, in the launch configuration bench.py times: the dislocation stress of
+    # the workload (GPU) relaxed for a few steps, every cell against the FP64 oracle's steps
+    # from the same FP32 load
+    p = W.CONFIGS[workload]()
+    g = p.geom
+    ctx = dds.context_for(p)
+    sig_d = ctx.stress(torch.from_numpy(p.rho.astype(np.float32)).cuda())
+    K = 3
+    u, tot = ctx.relax(sig_d, K)
+    torch.cuda.synchronize()
+    sig = sig_d.cpu().numpy().astype(np.float64)
+    h = (g.dx, g.dy, g.dz)
+    u_ref = R.relax(sig, h, g.mu, g.nu, K)
+    tot_ref = R.total_stress(u_ref, sig, h, g.mu, g.nu)
+    assert rel_l2(u.cpu().numpy(), u_ref) <= tol_step(K)
+    assert rel_l2_total(tot.cpu().numpy(), tot_ref) <= tol_step(K)
+    ctx.close()

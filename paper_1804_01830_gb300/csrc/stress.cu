@@ -195,17 +195,19 @@ cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in
   constexpr int W = YTile<PY>::W, T = YTile<PY>::NT;
   const long tiles = (long)nf * sh.nz * (sh.M / W) + (long)nf * ((sh.nz + W - 1) / W);
   if constexpr (INV && PY >= 1024) {
-    // 1024-row inverse: the shared-memory Stockham tile with 16-byte row stores
-    // (radial disk 512x512x16: 0.138 ms against 0.152 for the register stages)
+    // 1024-row inverse: the shared-memory Stockham tile with 16-byte row stores (radial
+    // disk 512x512x16: 0.137 ms, against 0.152 for the register stages on 4-column
+    // tiles and 0.146 on 8-column tiles of 256 threads)
     const size_t smem = sizeof(float2) * tile_elems<PY, W, Plan<PY>::r0, W>();
     cudaError_t err = prep(k_ypass<PY, W, T, INV>, smem);
     if (err != cudaSuccess) return err;
     k_ypass<PY, W, T, INV><<<(unsigned)tiles, T, smem, s>>>(sh, nf, im, in, om, on, tw);
     return cudaGetLastError();
   }
-  cudaError_t err = prep(yr::k_ypass_st<PY, W, T, INV>, 0);
+  const size_t smem = sizeof(float2) * yr::y_smem<PY, W>();
+  cudaError_t err = prep(yr::k_ypass_st<PY, W, T, INV>, smem);
   if (err != cudaSuccess) return err;
-  yr::k_ypass_st<PY, W, T, INV><<<(unsigned)tiles, T, 0, s>>>(sh, nf, im, in, om, on, tw);
+  yr::k_ypass_st<PY, W, T, INV><<<(unsigned)tiles, T, smem, s>>>(sh, nf, im, in, om, on, tw);
   return cudaGetLastError();
 }
 

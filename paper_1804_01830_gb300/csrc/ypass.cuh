@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(NT) k_ypass_st(Shape sh, int nf, const float2 
                                                  const float2 *__restrict__ in_nyq, float2 *__restrict__ out_main,
                                                  float2 *__restrict__ out_nyq, const float2 *__restrict__ tw) {
   constexpr int R1 = YCfg<PY>::R1, R2 = YCfg<PY>::R2, ST = y_stride<PY, W>();
-  __shared__ __align__(16) float2 sm[y_smem<PY, W>()];
+  extern __shared__ __align__(16) float2 sm[];              // y_smem<PY, W>() values
   const int tid = threadIdx.x;
   const int M = sh.M, nz = sh.nz;
   const int rows_in = INV ? PY : sh.ny;

@@ -464,14 +464,17 @@ def serving_benchmark(device: int, duration: float, rate: float = 200.0, budget:
 
 
 # ----------------------------------------------------------- CPU baseline --
-def oracle_sample(p, seconds: float, seed: int = 0):
-    """Time the FP64 oracle's direct sum on a bounded sample of target cells."""
+def oracle_sample(p, seconds: float, seed: int = 0, one: float | None = None):
+    """Time the FP64 oracle's direct sum on a bounded sample of target cells (about
+    `seconds` of work; `one` = the time of one target if already known)."""
     import oracle
     oracle.build()
     rng = np.random.default_rng(seed)
-    t0 = time.perf_counter()
-    oracle.stress_direct(p.geom, p.t, p.b, p.rho, targets=rng.integers(0, p.geom.n_cells, size=1), use_table=False)
-    one = max(time.perf_counter() - t0, 1e-3)
+    if one is None:
+        t0 = time.perf_counter()
+        oracle.stress_direct(p.geom, p.t, p.b, p.rho, targets=rng.integers(0, p.geom.n_cells, size=1),
+                             use_table=False)
+        one = max(time.perf_counter() - t0, 1e-3)
     n = int(max(1, min(4096, seconds / one)))
     tg = rng.integers(0, p.geom.n_cells, size=n)
     t0 = time.perf_counter()
@@ -485,12 +488,14 @@ def run_reference(args):
     if rank != 0:
         return 0
     p = W.CONFIGS[args.workload]()
-    per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
+    # about a minute of oracle work in all, at least one target cell per step
+    per_step = 60.0 / max(args.steps + args.warmup, 1)
+    n1, one, _ = oracle_sample(p, 0.0, seed=1)            # one target: its cost
     for _ in range(args.warmup):
-        oracle_sample(p, min(per_step, 2.0), seed=1)
+        oracle_sample(p, min(per_step, 2.0), seed=1, one=one)
     total_cells, total_s, cores = 0, 0.0, 1
     for k in range(args.steps):
-        n, dt, cores = oracle_sample(p, per_step, seed=100 + k)
+        n, dt, cores = oracle_sample(p, per_step, seed=100 + k, one=one)
         total_cells += n
         total_s += dt
     v = total_cells / total_s

@@ -72,6 +72,21 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
+    """The maximum of x over all ranks of the default process group (x itself alone)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Replicas: every rank processes units_per_rank; the job takes the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ clocks --
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -563,12 +578,8 @@ def run_ours(args):
     step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
     per_pass = dds.dds_profile_read(ctx.handle, K)
     dds.dds_profile_enable(ctx.handle, False)
-    total_ms = float(step_ms.sum())
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * g.n_cells * K / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(step_ms.sum()), dist, "cuda")
+    value = whole_job_rate(world, g.n_cells * K, total_ms / 1e3)
 
     # roofline of the dominant kernel, measured over the timed region
     pb = pass_bytes(p, q)
@@ -597,12 +608,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(ke):
             ctx.stress_host(rh, sh)
-        dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * g.n_cells * ke / dt, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": whole_job_rate(world, g.n_cells * ke, dt), "unit": UNIT,
                "h2d_bytes_per_step": int(rho_h.numel() * 4), "d2h_bytes_per_step": int(sig_h.numel() * 4),
                "steps": ke}
 

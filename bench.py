@@ -176,13 +176,22 @@ def measured_peaks():
         return {}
 
 
-def kernel_source_hash() -> str:
+# Sources that define each pass's kernels: a committed ncu traffic record stays valid
+# while these files are unchanged.
+KERNEL_SOURCES = {
+    "z_fused": ("zpass_impl.cuh", "zpass_f32.cu", "dds_fft.cuh", "stress_common.cuh"),
+    "x_fwd": ("xpass.cuh", "dds_fft.cuh", "stress_common.cuh"),
+    "x_inv": ("xpass.cuh", "bulk.cuh", "dds_fft.cuh", "stress_common.cuh"),
+    "y_fwd": ("ypass.cuh", "dds_fft.cuh", "stress_common.cuh"),
+    "y_inv": ("stress.cu", "ypass.cuh", "dds_fft.cuh", "stress_common.cuh"),
+}
+
+
+def kernel_source_hash(kernel: str = "z_fused") -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("paper_1804_01830_gb300/csrc/stress.cu", "paper_1804_01830_gb300/csrc/dds_fft.cuh",
-              "paper_1804_01830_gb300/csrc/xpass.cuh", "paper_1804_01830_gb300/csrc/stress_common.cuh",
-              "paper_1804_01830_gb300/csrc/zpass_impl.cuh"):
-        h.update((ROOT / f).read_bytes())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update((ROOT / "paper_1804_01830_gb300" / "csrc" / f).read_bytes())
     return h.hexdigest()[:16]
 
 
@@ -192,7 +201,7 @@ def ncu_traffic(kernel: str, workload: str):
     f = ROOT / "profiles" / "ncu_traffic.json"
     try:
         e = json.loads(f.read_text())[workload][kernel]
-        return float(e["dram_bytes_per_launch"]) if e["source_hash"] == kernel_source_hash() else None
+        return float(e["dram_bytes_per_launch"]) if e["source_hash"] == kernel_source_hash(kernel) else None
     except Exception:
         return None
 

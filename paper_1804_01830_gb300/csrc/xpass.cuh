@@ -346,6 +346,18 @@ __device__ __forceinline__ float2 load_pair(const void *rho, long o, int n2x, in
   return make_float2(r[o], n2x + 1 < nx ? r[o + 1] : 0.f);
 }
 
+// Four consecutive density values x[o .. o+3] (o a multiple of 4, row length a multiple
+// of 4): one 16-byte load (FP32) or one 8-byte load (BF16).
+template <bool BF16>
+__device__ __forceinline__ float4 load_quad(const void *rho, long o) {
+  if (BF16) {
+    const uint2 w = __ldg(reinterpret_cast<const uint2 *>((const uint16_t *)rho + o));
+    return make_float4(__uint_as_float(w.x << 16), __uint_as_float(w.x & 0xffff0000u),
+                       __uint_as_float(w.y << 16), __uint_as_float(w.y & 0xffff0000u));
+  }
+  return __ldcs(reinterpret_cast<const float4 *>((const float *)rho + o));
+}
+
 // Groups with one family and one field (DIRECT) transform that family scaled by its
 // coefficient; the others sum coef * rho over the group's families for each field.
 template <int M, bool BF16, bool DIRECT>
@@ -353,8 +365,12 @@ __global__ void __launch_bounds__(THREADS)
 k_x_fwd_reg(Shape sh, Collapse col, GroupList gl, const void *__restrict__ rho_v, float2 *__restrict__ out_main,
             float2 *__restrict__ out_nyq, const float2 *__restrict__ tw) {
   constexpr int R1 = FwdCfg<M>::R1, R2 = FwdCfg<M>::R2, T = R1 / 2, CPT = R2 / T, H = R1 / 2;
-  constexpr int LPB = THREADS / T, LD = R2 + 1, S = R1 * LD + line_pad<T>();
-  static_assert(R1 * R2 == M && CPT >= 1 && CPT * T == R2, "x forward config");
+  // thread t owns the adjacent columns n2 = CPT t + q; row stride and line shift keep
+  // the shared-memory stages free of bank conflicts (2-way left for M = 16, 64)
+  constexpr int LD = (M == 256) ? R2 + 2 : R2 + 1;
+  constexpr int PADL = (M == 256) ? 1 : (CPT == 1 ? line_pad<T>() : 0);
+  constexpr int LPB = THREADS / T, S = R1 * LD + PADL;
+  static_assert(R1 * R2 == M && CPT >= 1 && CPT * T == R2 && CPT <= 2, "x forward config");
   __shared__ float2 sm[LPB * S];
   const int t = threadIdx.x % T, lw = threadIdx.x / T;
   const long L = (long)sh.ny * sh.nz;
@@ -367,12 +383,13 @@ k_x_fwd_reg(Shape sh, Collapse col, GroupList gl, const void *__restrict__ rho_v
   const long set_off = (long)bset * sh.fin * N;
   const int nxh = (sh.nx + 1) >> 1;
   const bool even = (sh.nx & 1) == 0;
+  const bool quad = (sh.nx & 3) == 0;               // rows and column pairs 16-byte aligned
   const float2 *twM = tw + tw_offset(M);
   const float2 *tw2 = tw + tw_offset(2 * M);
   const int ra = t, rb = t0 ? R1 / 2 : R1 - t;
   float2 *ls = sm + lw * S;
 
-  // stage-1 inputs z[n2 + R2 n1], n2 = t + T q, n1 < R1 / 2, of every field of the
+  // stage-1 inputs z[n2 + R2 n1], n2 = CPT t + q, n1 < R1 / 2, of every field of the
   // group: each family is read once and added into all fields (coef * rho).
   constexpr int NDM = DIRECT ? 1 : 3;
   const int nd = col.nd[g];
@@ -390,13 +407,27 @@ k_x_fwd_reg(Shape sh, Collapse col, GroupList gl, const void *__restrict__ rho_v
       const int fi = col.f0[g] + f;
       const long base = set_off + (long)col.fam[fi] * N + line * sh.nx;
       float2 v[CPT][H];
-#pragma unroll
-      for (int q = 0; q < CPT; ++q)
+      if (CPT == 2 && quad) {                 // both columns' pairs in one 16-byte (8 for bf16) load
 #pragma unroll
         for (int n1 = 0; n1 < H; ++n1) {
-          const int n = t + T * q + R2 * n1;
-          v[q][n1] = n < nxh ? load_pair<BF16>(rho_v, base + 2 * n, 2 * n, sh.nx, even) : make_float2(0.f, 0.f);
+          const int n = CPT * t + R2 * n1;    // even; nxh even, so n + 1 < nxh with n
+          if (n < nxh) {
+            const float4 x = load_quad<BF16>(rho_v, base + 2 * n);
+            v[0][n1] = make_float2(x.x, x.y);
+            v[CPT - 1][n1] = make_float2(x.z, x.w);
+          } else {
+            v[0][n1] = v[CPT - 1][n1] = make_float2(0.f, 0.f);
+          }
         }
+      } else {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q)
+#pragma unroll
+          for (int n1 = 0; n1 < H; ++n1) {
+            const int n = CPT * t + q + R2 * n1;
+            v[q][n1] = n < nxh ? load_pair<BF16>(rho_v, base + 2 * n, 2 * n, sh.nx, even) : make_float2(0.f, 0.f);
+          }
+      }
       if (DIRECT) {
 #pragma unroll
         for (int q = 0; q < CPT; ++q)
@@ -428,7 +459,7 @@ k_x_fwd_reg(Shape sh, Collapse col, GroupList gl, const void *__restrict__ rho_v
     if (d > 0) __syncthreads();                      // previous field's stage 2 has read ls
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
-      const int n2 = t + T * q;
+      const int n2 = CPT * t + q;
       float2 ev[H], od[H];
 #pragma unroll
       for (int n1 = 0; n1 < H; ++n1) {

@@ -119,6 +119,8 @@ def test_gaussian_disk_32_full(dds):
     ((250, 5, 2), (1e-6, 1e-6, 0.25e-6), [1, 6, 12], 10),                 # M = 256
     ((300, 3, 2), (0.5e-6, 0.5e-6, 0.2e-6), [7, 14], 11),                 # M = 512
     ((17, 5, 4), (0.2e-6, 0.2e-6, 0.05e-6), [5], 12),                     # M = 32, odd nx, one family
+    ((244, 7, 3), (0.2e-6, 0.2e-6, 0.05e-6), [0, 3, 9, 14], 13),          # M = 256, 4-value loads, summed
+    ((12, 9, 5), (1e-6, 1e-6, 0.25e-6), [6], 14),                         # M = 16, 4-value loads
 ])
 def test_random_densities_vs_direct_sum(dds, shape, cells, fams, seed):
     g = W.Geometry(*shape, *cells)
@@ -189,7 +191,9 @@ def test_linearity_at_full_size(dds):
 
 
 @pytest.mark.parametrize("shape,fams", [((24, 20, 8), [0, 9]),              # one family per group
-                                        ((33, 10, 5), [0, 1, 2, 9, 10])])    # summed families, odd nx
+                                        ((33, 10, 5), [0, 1, 2, 9, 10]),     # summed families, odd nx
+                                        ((200, 6, 3), [0, 1, 9, 10]),        # M = 256, 4-value loads
+                                        ((48, 10, 4), [2, 9])])              # M = 64, 4-value loads
 def test_bf16_density_storage(dds, shape, fams):
     p = W.random_problem(W.Geometry(*shape, 0.2e-6, 0.2e-6, 0.05e-6), *[a[fams] for a in W.gan_families()],
                          seed=11)

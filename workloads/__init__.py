@@ -253,6 +253,14 @@ def gan_layer_256(seed: int = 0) -> Problem:
     return gan_polycrystal(g, 2.0 * UM, seed, name="gan_layer_256x256x128")
 
 
+def gan_layer_128(seed: int = 0) -> Problem:
+    """The GaN layer's cells, grains, families and height profile on a 128x128x128 grid
+    (one of the sweep grids): the same padded z size with a quarter of the columns, for
+    profiling captures that must stay small."""
+    g = Geometry(128, 128, 128, 0.2 * UM, 0.2 * UM, 0.05 * UM)
+    return gan_polycrystal(g, 2.0 * UM, seed, name="gan_layer_128x128x128")
+
+
 SWEEP_GRIDS = [(128, 128, 64), (128, 128, 128), (256, 256, 64), (256, 256, 128)]
 
 
@@ -381,4 +389,5 @@ CONFIGS = {
     "gaussian_disk_32x32x8": gaussian_disk_32,
     "radial_disk_512x512x16": radial_disk_512,
     "gan_layer_256x256x128": gan_layer_256,
+    "gan_layer_128x128x128": gan_layer_128,
 }

@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-reduced", action="store_true", help="skip the FP16-spectra measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency measurement")
     ap.add_argument("--serving-seconds", type=float, default=5.0)
+    ap.add_argument("--serving-streams", type=int, default=4, help="CUDA streams of the server")
+    ap.add_argument("--serving-batch", type=int, default=2, help="largest batch per context")
     ap.add_argument("--no-autotune", action="store_true", help="use the planner's default z schedule")
     ap.add_argument("--no-relax", action="store_true", help="skip the free-surface relaxation measurement")
     ap.add_argument("--no-grain", action="store_true", help="skip the grain-size scaling study")
@@ -423,7 +425,8 @@ def sweep_benchmark(device: int, n_real: int = 64, reps: int = 5, oracle_targets
     return out
 
 
-def serving_benchmark(device: int, duration: float, rate: float = 200.0, budget: float = 150e9, seed: int = 0):
+def serving_benchmark(device: int, duration: float, rate: float = 200.0, budget: float = 150e9, seed: int = 0,
+                      n_streams: int = 4, max_batch: int = 2):
     """Poisson stream of stress requests (mixed grids, cell aspects and family sets)
     through the continuous-batching server; kernel spectra cached per geometry (warmed
     before the timed stream), admission by an HBM budget.  Latency = submission to the
@@ -446,7 +449,7 @@ def serving_benchmark(device: int, duration: float, rate: float = 200.0, budget:
         g = c.geom
         return StressRequest((g.nx, g.ny, g.nz), (g.dx, g.dy, g.dz), g.mu, g.nu, c.t, c.b, dens[(kind[0], kind[2])])
 
-    srv = StressServer(device=device, hbm_budget=budget, n_streams=4, max_batch=2)
+    srv = StressServer(device=device, hbm_budget=budget, n_streams=n_streams, max_batch=max_batch)
     t0 = time.perf_counter()
     for kind in kinds:
         srv.warm(request(kind))
@@ -484,7 +487,8 @@ def serving_benchmark(device: int, duration: float, rate: float = 200.0, budget:
             "family_sets": W.SERVING_FAMILY_SETS, "contexts": len(kinds), "kernel_build_s": build_s,
             "p50_ms": lat.get("p50"), "p99_ms": lat.get("p99"), "mean_ms": lat.get("mean"),
             "max_ms": lat.get("max"), "throughput_req_per_s": len(arrivals) / wall,
-            "cells_per_s": cells / wall, "hbm_budget_gb": budget / 1e9}
+            "cells_per_s": cells / wall, "hbm_budget_gb": budget / 1e9, "streams": n_streams,
+            "max_batch": max_batch}
 
 
 # ----------------------------------------------------------- CPU baseline --
@@ -662,7 +666,8 @@ def run_ours(args):
 
     serving = None
     if not args.no_serving and rank == 0 and world == 1:
-        serving = serving_benchmark(local, args.serving_seconds)
+        serving = serving_benchmark(local, args.serving_seconds, n_streams=args.serving_streams,
+                                    max_batch=args.serving_batch)
 
     comparator = None
     if not args.no_comparator:

@@ -9,10 +9,9 @@ namespace dds {
 
 constexpr int NT = 256;   // threads of the shared-memory z pass
 
-// Tile shapes of the x and y passes: W lines (columns) per tile, NT threads.
-// Small tiles keep several CTAs resident per SM so that one tile's copies overlap
-// another tile's transform.
-template <int P> struct XTile { static constexpr int W = 16, NT = 256; };
+// Tile shape of the y passes: W columns per tile, NT threads.  Small tiles keep
+// several CTAs resident per SM so that one tile's copies overlap another tile's
+// transform.
 template <int P> struct YTile { static constexpr int W = P >= 1024 ? 4 : (P >= 512 ? 8 : 16), NT = 128; };
 
 __device__ __forceinline__ float2 cmadd_i(float2 acc, float g, float2 r) {

@@ -332,6 +332,38 @@ def grain_scaling_study(device: int):
     return out
 
 
+def small_grid_latency(device: int, iters: int = 1000):
+    """The 32x32x8 Gaussian disk (first configuration): 8192 cells, launch-bound.  Time
+    per evaluation launched directly (five kernels) and replayed as a captured CUDA graph
+    of one evaluation, both averaged over `iters` back-to-back evaluations."""
+    import numpy as np
+    import torch
+    import paper_1804_01830_gb300 as dds
+    p = W.gaussian_disk_32()
+    ctx = dds.context_for(p, device=device)
+    rho = torch.from_numpy(p.rho.astype(np.float32)).to(f"cuda:{device}")
+    sigma = torch.empty((6,) + p.geom.shape, dtype=torch.float32, device=rho.device)
+    graph = dds.StressGraph([(ctx, rho[None].contiguous())])
+    out = {"workload": "gaussian_disk_32x32x8", "cells": p.geom.n_cells, "iters": iters}
+    for name, run in (("direct", lambda: ctx.stress(rho, sigma)), ("graph", graph.launch)):
+        for _ in range(20):
+            run()
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(iters):
+            run()
+        e1.record()
+        torch.cuda.synchronize(device)
+        out[f"{name}_us_per_evaluation"] = 1e3 * e0.elapsed_time(e1) / iters
+    same = torch.equal(graph.sigma[0][0], ctx.stress(rho, sigma))
+    torch.cuda.synchronize(device)
+    out["graph_equals_direct"] = bool(same)
+    graph.close()
+    ctx.close()
+    return out
+
+
 def sweep_benchmark(device: int, n_real: int = 64, reps: int = 5, oracle_targets: int = 6):
     """The batched grain-size sweep: n_real polycrystal realisations on the four sweep
     grids (cells 0.2x0.2x0.05 um, 18 families, grain diameters log-uniform in 0.5-8 um),
@@ -663,6 +695,7 @@ def run_ours(args):
     sweep = None
     if not args.no_sweep and rank == 0 and world == 1:
         sweep = sweep_benchmark(local)
+        sweep["small_grid_latency"] = small_grid_latency(local)
 
     serving = None
     if not args.no_serving and rank == 0 and world == 1:

@@ -130,14 +130,20 @@ class StressServer:
         dx, dy, dz = req.cells
         ctx.set_geometry(nx, ny, nz, dx, dy, dz, req.mu, req.nu).set_families(req.t, req.b)
         ctx.build_kernels(self.streams[0])
+        torch = self.torch
         if self.max_batch > 1:
             # size the work buffers for a full batch now (growing them later synchronises the device)
-            torch = self.torch
             with torch.cuda.stream(self.streams[0]):
                 z = torch.zeros((self.max_batch, len(req.t), nz, ny, nx), device=f"cuda:{self.device}")
                 ctx.stress_multi(z, stream=self.streams[0])
             self.streams[0].synchronize()
             del z
+        # pinned host buffers for the results of as many batches as there are streams:
+        # allocated and released here so that the host allocator keeps them cached,
+        # instead of allocating them on this thread while requests wait
+        outs = [torch.empty((self.max_batch, 6, nz, ny, nx), dtype=torch.float32, pin_memory=True)
+                for _ in range(len(self.streams))]
+        del outs
         e = _Entry(ctx, context_bytes(ctx.query(), req.grid, len(req.t), self.max_batch))
         self.cache[req.key()] = e
         self.resident += e.nbytes

@@ -20,6 +20,63 @@ __device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
 // (fe x PZ x W values) stream into one of two buffers G by cp.async while the
 // previous component is contracted, and while the inverse FFTs run; the six
 // components are formed in S[z][c' W + w] and inverted three at a time.
+// The inverse z transform of three components (3W lines of S, rows kz < PZ) in two
+// register stages of PZ = R1 R2 (four-step factorisation), the second storing rows
+// z < nz straight to global memory: S is read twice and written once, against the
+// four sweeps and the copy-out of a Stockham tile.  The stage-1 results go back into S
+// (after a barrier), transposed, with a row stride that keeps both stages free of bank
+// conflicts; S holds PZ 3W + R1 ZPAD values.
+template <int W> __host__ __device__ constexpr int zpad() { return W == 8 ? 8 : 3 * W; }
+template <int PZ, int W> __host__ __device__ constexpr bool z_reg_inverse() { return Plan<PZ>::n == 2 && W <= 8; }
+template <int PZ, int W> __host__ __device__ constexpr int z_s_extra() {
+  return z_reg_inverse<PZ, W>() ? Plan<PZ>::r0 * zpad<W>() : 0;
+}
+
+template <int PZ, int W, typename Store>
+__device__ __forceinline__ void inverse3_store(float2 *S, const float2 *twP, int tid, int nz, Store store) {
+  constexpr int R1 = Plan<PZ>::r0, R2 = Plan<PZ>::r1, L3 = 3 * W, ST = R2 * L3 + zpad<W>();
+  constexpr int I1 = (R2 * L3 + NT - 1) / NT, I2 = (R1 * L3 + NT - 1) / NT;
+  float2 v[I1][R1];
+#pragma unroll
+  for (int it = 0; it < I1; ++it) {
+    const int item = tid + it * NT;
+    if ((R2 * L3) % NT != 0 && item >= R2 * L3) continue;
+    const int n2 = item / L3, line = item - n2 * L3;
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[it][n1] = S[(n2 + R2 * n1) * L3 + line];
+  }
+  __syncthreads();                            // S read: it now takes the stage-1 results
+#pragma unroll
+  for (int it = 0; it < I1; ++it) {
+    const int item = tid + it * NT;
+    if ((R2 * L3) % NT != 0 && item >= R2 * L3) continue;
+    const int n2 = item / L3, line = item - n2 * L3;
+    dft_reg<R1, true>(v[it]);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      float2 y = v[it][k1];
+      if (k1 > 0) y = cmul_tw<true>(y, __ldg(twP + n2 * k1));
+      S[k1 * ST + n2 * L3 + line] = y;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < I2; ++it) {
+    const int item = tid + it * NT;
+    if ((R1 * L3) % NT != 0 && item >= R1 * L3) continue;
+    const int k1 = item / L3, line = item - k1 * L3;
+    float2 y[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) y[n2] = S[k1 * ST + n2 * L3 + line];
+    dft_reg<R2, true>(y);
+#pragma unroll
+    for (int k2 = 0; k2 < R2 / 2; ++k2) {
+      const int z = k1 + R1 * k2;
+      if (z < nz) store(line, z, y[k2]);
+    }
+  }
+}
+
 template <int PZ, int W, int FEMAX, typename GT>
 __global__ void __launch_bounds__(NT) k_zpass(Shape sh, const float2 *in_main, const float2 *in_nyq,
                                               const GT *kspec, const float *kscale, float2 *out_main,
@@ -32,7 +89,7 @@ __global__ void __launch_bounds__(NT) k_zpass(Shape sh, const float2 *in_main, c
   const int L = fe * W;
   float2 *F = smem;                                       // [PZ][fe W]
   float2 *S = smem + (long)PZ * L;                        // [PZ][3 W]
-  GT *G0 = reinterpret_cast<GT *>(S + 3 * TS);           // [fe][PZ][W], two buffers
+  GT *G0 = reinterpret_cast<GT *>(S + 3 * TS + z_s_extra<PZ, W>());   // [fe][PZ][W], two buffers
   GT *G1 = G0 + (long)fe * TS;
   const long ktiles = M / W;
   const long tiles_main = (long)py * ktiles;
@@ -100,11 +157,19 @@ __global__ void __launch_bounds__(NT) k_zpass(Shape sh, const float2 *in_main, c
     }
     if (c3 == 2) {
       __syncthreads();
-      fft_tile_rt<PZ, 3 * W, NT, true, false, true>(S, 3 * W, twP, tid);
-      for (int p = tid; p < nz * 3 * W; p += NT) {
-        const int z = p / (3 * W), r = p - z * (3 * W), cc = c - 2 + r / W, w = r % W;
-        if (!nyq) out_main[(((long)cc * nz + z) * py + ky) * M + kx0 + w] = S[p];
-        else out_nyq[((long)cc * py + ky0 + w) * nz + z] = S[p];
+      if constexpr (z_reg_inverse<PZ, W>()) {
+        inverse3_store<PZ, W>(S, twP, tid, nz, [&](int line, int z, float2 val) {
+          const int cc = c - 2 + line / W, w = line % W;
+          if (!nyq) out_main[(((long)cc * nz + z) * py + ky) * M + kx0 + w] = val;
+          else out_nyq[((long)cc * py + ky0 + w) * nz + z] = val;
+        });
+      } else {
+        fft_tile_rt<PZ, 3 * W, NT, true, false, true>(S, 3 * W, twP, tid);
+        for (int p = tid; p < nz * 3 * W; p += NT) {
+          const int z = p / (3 * W), r = p - z * (3 * W), cc = c - 2 + r / W, w = r % W;
+          if (!nyq) out_main[(((long)cc * nz + z) * py + ky) * M + kx0 + w] = S[p];
+          else out_nyq[((long)cc * py + ky0 + w) * nz + z] = S[p];
+        }
       }
     }
   }
@@ -309,7 +374,8 @@ __global__ void __launch_bounds__(128) k_zreg(Shape sh, const float2 *in_main, c
 template <int PZ, int W, int FEMAX, typename GT>
 cudaError_t launch_z_fe(const Shape &sh, const float2 *im, const float2 *in, const GT *ks, const float *ksc,
                         float2 *om, float2 *on, const float2 *tw, cudaStream_t s) {
-  const size_t smem = (sizeof(float2) * (size_t)(sh.fe + 3) + 2 * sizeof(GT) * (size_t)sh.fe) * PZ * W;
+  const size_t smem = (sizeof(float2) * (size_t)(sh.fe + 3) + 2 * sizeof(GT) * (size_t)sh.fe) * PZ * W +
+                      sizeof(float2) * z_s_extra<PZ, W>();
   const long tiles = ((long)sh.py * (sh.M / W) + sh.py / W) * sh.nb;
   cudaError_t err = prep(k_zpass<PZ, W, FEMAX, GT>, smem);
   if (err != cudaSuccess) return err;

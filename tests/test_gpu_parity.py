@@ -158,19 +158,57 @@ def sample_targets(g, n, seed):
     return np.unique(np.concatenate([pts, corners]))
 
 
+def x_line(g, y, z):
+    """Linear indices of the full x-line at (y, z)."""
+    return z * g.nx * g.ny + y * g.nx + np.arange(g.nx)
+
+
 def test_radial_disk_512_sampled(dds):
+    # 96 random cells, the corners, and one full x-line through the disk centre
     p = W.radial_disk_512()
     got = gpu_stress(dds, p).reshape(6, -1)
-    tg = sample_targets(p.geom, 24, seed=1)
-    ref = oracle.stress_direct(p.geom, p.t, p.b, p.rho, targets=tg, use_table=False).T
+    g = p.geom
+    tg = np.unique(np.concatenate([sample_targets(g, 96, seed=1), x_line(g, g.ny // 2, g.nz // 2)]))
+    ref = oracle.stress_direct(g, p.t, p.b, p.rho, targets=tg, use_table=False).T
     assert rel_l2_per_component(got[:, tg], ref).max() <= TOL_STRESS
 
 
 def test_gan_layer_256_sampled(dds):
+    # 48 random cells, the corners, and one full x-line in the dense bottom layers
     p = W.gan_layer_256(0)
     got = gpu_stress(dds, p).reshape(6, -1)
-    tg = sample_targets(p.geom, 12, seed=2)
-    ref = oracle.stress_direct(p.geom, p.t, p.b, p.rho, targets=tg, use_table=False).T
+    g = p.geom
+    tg = np.unique(np.concatenate([sample_targets(g, 48, seed=2), x_line(g, 101, 3)]))
+    ref = oracle.stress_direct(g, p.t, p.b, p.rho, targets=tg, use_table=False).T
+    assert rel_l2_per_component(got[:, tg], ref).max() <= TOL_STRESS
+
+
+@pytest.mark.parametrize("r", [3, 5])
+def test_sweep_realisation_sampled(dds, r):
+    # the grain-size sweep (grid and grain diameter drawn per realisation), FP32 and BF16
+    # densities; BF16 against the oracle on the bf16-rounded densities
+    p = W.sweep_realisation(r)
+    g = p.geom
+    tg = np.unique(np.concatenate([sample_targets(g, 24, seed=r), x_line(g, g.ny // 3, 1)[::4]]))
+    got = gpu_stress(dds, p).reshape(6, -1)
+    ref = oracle.stress_direct(g, p.t, p.b, p.rho, targets=tg, use_table=False).T
+    assert rel_l2_per_component(got[:, tg], ref).max() <= TOL_STRESS
+    got16 = gpu_stress(dds, p, dtype=torch.bfloat16).reshape(6, -1)
+    rho16 = torch.from_numpy(p.rho.astype(np.float32)).to(torch.bfloat16).float().double().numpy()
+    t16 = tg[::3]
+    ref16 = oracle.stress_direct(g, p.t, p.b, rho16, targets=t16, use_table=False).T
+    assert rel_l2_per_component(got16[:, t16], ref16).max() <= TOL_STRESS
+
+
+@pytest.mark.parametrize("kind", [(0, 0, 1), (1, 1, 0), (3, 2, 1)])
+def test_serving_kinds_sampled(dds, kind):
+    # request kinds of the serving mix: grid, cell aspect dz/dx, family set
+    c = W.serving_problem(*kind, seed=0)
+    p = W.Problem("serving", c.geom, c.t, c.b, c.rho.astype(np.float64))
+    g = p.geom
+    tg = np.unique(np.concatenate([sample_targets(g, 24, seed=7), x_line(g, g.ny // 2, 0)[::4]]))
+    got = gpu_stress(dds, p).reshape(6, -1)
+    ref = oracle.stress_direct(g, p.t, p.b, p.rho, targets=tg, use_table=False).T
     assert rel_l2_per_component(got[:, tg], ref).max() <= TOL_STRESS
 
 

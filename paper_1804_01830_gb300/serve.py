@@ -44,8 +44,13 @@ class StressRequest:
     submitted: float = field(default=0.0)
 
     def key(self):
-        return (tuple(int(v) for v in self.grid), tuple(float(v) for v in self.cells), float(self.mu),
-                float(self.nu), np.asarray(self.t, np.float64).tobytes(), np.asarray(self.b, np.float64).tobytes())
+        """Identity of the geometry and family set (one cached context per key)."""
+        k = self.__dict__.get("_key")
+        if k is None:
+            k = (tuple(int(v) for v in self.grid), tuple(float(v) for v in self.cells), float(self.mu),
+                 float(self.nu), np.asarray(self.t, np.float64).tobytes(), np.asarray(self.b, np.float64).tobytes())
+            self.__dict__["_key"] = k
+        return k
 
 
 class _Entry:
@@ -201,15 +206,16 @@ class StressServer:
         progressed = True
         while progressed and self.pending and self.free_streams:
             progressed = False
-            for idx, (req, fut) in enumerate(self.pending):
+            for req, fut in self.pending:
                 entry = self._get_entry(req)
                 if entry is not None and entry.busy:
                     continue                       # its context is on the GPU; try others
                 k = req.key()
                 group = [(r, f) for r, f in self.pending if r.key() == k][: self.max_batch]
-                need = self._io_bytes([r for r, _ in group]) + (0 if entry else 0)
+                need = self._io_bytes([r for r, _ in group])
                 if entry is None:
-                    # footprint of a new context is known after planning; build then account
+                    # a new context's own footprint is known once it is built: make room for
+                    # the request's buffers, build (which accounts the context), then re-check
                     if not self._make_room(need):
                         continue
                     entry = self._build_entry(req)

@@ -687,6 +687,9 @@ def run_ours(args):
     # serving first among the extra sections: a clean device and host allocator state
     serving = None
     if not args.no_serving and rank == 0 and world == 1:
+        import gc
+        gc.collect()
+        torch.cuda.empty_cache()
         serving = serving_benchmark(local, args.serving_seconds, n_streams=args.serving_streams,
                                     max_batch=args.serving_batch)
 

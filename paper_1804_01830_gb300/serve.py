@@ -143,12 +143,18 @@ class StressServer:
                 ctx.stress_multi(z, stream=self.streams[0])
             self.streams[0].synchronize()
             del z
-        # pinned host buffers for the results of as many batches as there are streams:
-        # allocated and released here so that the host allocator keeps them cached,
-        # instead of allocating them on this thread while requests wait
-        outs = [torch.empty((self.max_batch, 6, nz, ny, nx), dtype=torch.float32, pin_memory=True)
+        # buffers for as many batches as there are streams -- pinned host results, and on
+        # each stream the device densities and stresses -- allocated and released here so
+        # that the allocators keep them cached, instead of allocating on this thread while
+        # requests wait
+        dev = f"cuda:{self.device}"
+        keep = [torch.empty((self.max_batch, 6, nz, ny, nx), dtype=torch.float32, pin_memory=True)
                 for _ in range(len(self.streams))]
-        del outs
+        for st in self.streams:
+            with torch.cuda.stream(st):
+                keep.append(torch.empty((self.max_batch, len(req.t), nz, ny, nx), dtype=torch.float32, device=dev))
+                keep.append(torch.empty((self.max_batch, 6, nz, ny, nx), dtype=torch.float32, device=dev))
+        del keep
         e = _Entry(ctx, context_bytes(ctx.query(), req.grid, len(req.t), self.max_batch))
         self.cache[req.key()] = e
         self.resident += e.nbytes

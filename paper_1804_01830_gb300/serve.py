@@ -29,7 +29,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import DDS_F32, StressContext
+from . import StressContext
 
 
 @dataclass(eq=False)
@@ -71,19 +71,95 @@ def context_bytes(q: dict, grid, n_families: int, nb: int = 1) -> int:
     return spectra + (a + b) * 8 + (2 << 20)
 
 
-class StressServer:
-    def __init__(self, device: int = 0, hbm_budget: float = 150e9, n_streams: int = 4, max_batch: int = 8):
+class CudaBackend:
+    """The device side of the server: contexts, streams, launches and their results.
+
+    The scheduler (StressServer) only calls these methods, so its admission, batching
+    and eviction logic can run against another backend (the CPU tests use a fake)."""
+
+    def __init__(self, device: int, n_streams: int, max_batch: int):
         import torch
         self.torch = torch
         self.device = device
-        self.budget = float(hbm_budget)
         self.max_batch = max_batch
         self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
+
+    def build(self, req: StressRequest):
+        """A built context for the request's geometry and families, and its device bytes."""
+        torch = self.torch
+        ctx = StressContext(self.device)
+        nx, ny, nz = req.grid
+        dx, dy, dz = req.cells
+        ctx.set_geometry(nx, ny, nz, dx, dy, dz, req.mu, req.nu).set_families(req.t, req.b)
+        ctx.build_kernels(self.streams[0])
+        if self.max_batch > 1:
+            # size the work buffers for a full batch now (growing them later synchronises the device)
+            with torch.cuda.stream(self.streams[0]):
+                z = torch.zeros((self.max_batch, len(req.t), nz, ny, nx), device=f"cuda:{self.device}")
+                ctx.stress_multi(z, stream=self.streams[0])
+            self.streams[0].synchronize()
+            del z
+        # buffers for as many batches as there are streams -- pinned host results, and on
+        # each stream the device densities and stresses -- allocated and released here so
+        # that the allocators keep them cached, instead of allocating on the scheduler
+        # thread while requests wait
+        dev = f"cuda:{self.device}"
+        keep = [torch.empty((self.max_batch, 6, nz, ny, nx), dtype=torch.float32, pin_memory=True)
+                for _ in range(len(self.streams))]
+        for st in self.streams:
+            with torch.cuda.stream(st):
+                keep.append(torch.empty((self.max_batch, len(req.t), nz, ny, nx), dtype=torch.float32, device=dev))
+                keep.append(torch.empty((self.max_batch, 6, nz, ny, nx), dtype=torch.float32, device=dev))
+        del keep
+        return ctx, context_bytes(ctx.query(), req.grid, len(req.t), self.max_batch)
+
+    def launch(self, ctx, reqs, stream):
+        """Enqueue one batch on `stream`: densities in, stress_multi, results to pinned host
+        memory.  Returns a job handle for ready() / results()."""
+        torch = self.torch
+        with torch.cuda.stream(stream):
+            rho = torch.empty((len(reqs),) + tuple(reqs[0].rho.shape), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+            for i, r in enumerate(reqs):
+                rho[i].copy_(r.rho, non_blocking=True)
+            sigma = ctx.stress_multi(rho, stream=stream)
+            out = torch.empty(sigma.shape, dtype=sigma.dtype, pin_memory=True)
+            out.copy_(sigma, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return {"event": ev, "keep": (rho, sigma), "out": out}
+
+    @staticmethod
+    def ready(job) -> bool:
+        return job["event"].query()
+
+    @staticmethod
+    def results(job):
+        """Per request of the batch, sigma (6, nz, ny, nx) as a view of the pinned buffer."""
+        out = job["out"].numpy()
+        return [out[i] for i in range(out.shape[0])]
+
+    def pin(self, rho: np.ndarray):
+        return self.torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float32)).pin_memory()
+
+    @staticmethod
+    def close_context(ctx):
+        ctx.close()
+
+
+class StressServer:
+    def __init__(self, device: int = 0, hbm_budget: float = 150e9, n_streams: int = 4, max_batch: int = 8,
+                 backend=None):
+        self.backend = backend if backend is not None else CudaBackend(device, n_streams, max_batch)
+        self.device = device
+        self.budget = float(hbm_budget)
+        self.max_batch = max_batch
+        self.streams = list(self.backend.streams)
         self.free_streams = list(self.streams)
         self.cache: "OrderedDict[tuple, _Entry]" = OrderedDict()
         self.resident = 0
         self.pending: list = []            # (request, future)
-        self.inflight: list = []           # dicts: event, stream, entry, items, sigma
+        self.inflight: list = []           # dicts: job, stream, entry, items, io
         self.inbox: "queue.Queue" = queue.Queue()
         self.latencies: list = []
         self.stop_flag = False
@@ -96,7 +172,7 @@ class StressServer:
         """Queue a request; the future yields sigma (6, nz, ny, nx) as a numpy array."""
         fut: Future = Future()
         if isinstance(req.rho, np.ndarray):
-            req.rho = self.torch.from_numpy(np.ascontiguousarray(req.rho, dtype=np.float32)).pin_memory()
+            req.rho = self.backend.pin(req.rho)
         req.submitted = time.perf_counter()
         self.inbox.put((req, fut))
         return fut
@@ -105,7 +181,7 @@ class StressServer:
         self.stop_flag = True
         self.thread.join()
         for e in self.cache.values():
-            e.ctx.close()
+            self.backend.close_context(e.ctx)
         self.cache.clear()
 
     def __enter__(self):
@@ -116,9 +192,11 @@ class StressServer:
 
     def warm(self, req: StressRequest):
         """Build (and cache) the context of a request ahead of time (synchronous)."""
-        done = threading.Event()
-        self.inbox.put(("warm", req, done))
+        done, err = threading.Event(), []
+        self.inbox.put(("warm", req, done, err))
         done.wait()
+        if err:
+            raise err[0]
 
     # ------------------------------------------------------------- scheduler --
     def _get_entry(self, req: StressRequest):
@@ -130,80 +208,71 @@ class StressServer:
         return None
 
     def _build_entry(self, req: StressRequest):
-        ctx = StressContext(self.device)
-        nx, ny, nz = req.grid
-        dx, dy, dz = req.cells
-        ctx.set_geometry(nx, ny, nz, dx, dy, dz, req.mu, req.nu).set_families(req.t, req.b)
-        ctx.build_kernels(self.streams[0])
-        torch = self.torch
-        if self.max_batch > 1:
-            # size the work buffers for a full batch now (growing them later synchronises the device)
-            with torch.cuda.stream(self.streams[0]):
-                z = torch.zeros((self.max_batch, len(req.t), nz, ny, nx), device=f"cuda:{self.device}")
-                ctx.stress_multi(z, stream=self.streams[0])
-            self.streams[0].synchronize()
-            del z
-        # buffers for as many batches as there are streams -- pinned host results, and on
-        # each stream the device densities and stresses -- allocated and released here so
-        # that the allocators keep them cached, instead of allocating on this thread while
-        # requests wait
-        dev = f"cuda:{self.device}"
-        keep = [torch.empty((self.max_batch, 6, nz, ny, nx), dtype=torch.float32, pin_memory=True)
-                for _ in range(len(self.streams))]
-        for st in self.streams:
-            with torch.cuda.stream(st):
-                keep.append(torch.empty((self.max_batch, len(req.t), nz, ny, nx), dtype=torch.float32, device=dev))
-                keep.append(torch.empty((self.max_batch, 6, nz, ny, nx), dtype=torch.float32, device=dev))
-        del keep
-        e = _Entry(ctx, context_bytes(ctx.query(), req.grid, len(req.t), self.max_batch))
+        ctx, nbytes = self.backend.build(req)
+        e = _Entry(ctx, nbytes)
         self.cache[req.key()] = e
         self.resident += e.nbytes
         return e
 
-    def _make_room(self, need: float) -> bool:
+    def _make_room(self, need: float, keep=None) -> bool:
+        """Evict idle contexts other than `keep`, least recently used first, until `need`
+        more bytes fit."""
         while self.resident + need > self.budget:
-            victim = next((k for k, e in self.cache.items() if not e.busy), None)
+            victim = next((k for k, e in self.cache.items() if not e.busy and k != keep), None)
             if victim is None:
                 return False
             e = self.cache.pop(victim)
             self.resident -= e.nbytes
-            e.ctx.close()
+            self.backend.close_context(e.ctx)
         return True
 
-    def _io_bytes(self, reqs):
-        return sum(4 * r.rho.numel() * (1 + 6 / max(len(r.t), 1)) for r in reqs)
+    def _fit(self, group, keep):
+        """The longest prefix of `group` whose buffers fit the budget once idle contexts
+        other than `keep` are evicted."""
+        n = len(group)
+        while n > 0 and not self._make_room(self._io_bytes([r for r, _ in group[:n]]), keep):
+            n -= 1
+        return group[:n]
+
+    def _reject(self, key, ex):
+        """Fail every waiting request of `key` and drop its (idle) context."""
+        for r, fut in self.pending:
+            if r.key() == key and not fut.done():
+                fut.set_exception(ex)
+        self.pending = [x for x in self.pending if x[0].key() != key]
+        e = self.cache.get(key)
+        if e is not None and not e.busy:
+            del self.cache[key]
+            self.resident -= e.nbytes
+            self.backend.close_context(e.ctx)
+
+    @staticmethod
+    def _io_bytes(reqs):
+        return sum(4 * int(np.prod(tuple(r.rho.shape))) * (1 + 6 / max(len(r.t), 1)) for r in reqs)
 
     def _launch(self, entry: _Entry, items):
-        torch = self.torch
         stream = self.free_streams.pop()
         reqs = [r for r, _ in items]
-        with torch.cuda.stream(stream):
-            rho = torch.empty((len(reqs),) + tuple(reqs[0].rho.shape), dtype=torch.float32,
-                              device=f"cuda:{self.device}")
-            for i, r in enumerate(reqs):
-                rho[i].copy_(r.rho, non_blocking=True)
-            sigma = entry.ctx.stress_multi(rho, stream=stream)
-            out = torch.empty(sigma.shape, dtype=sigma.dtype, pin_memory=True)
-            out.copy_(sigma, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(stream)
+        job = self.backend.launch(entry.ctx, reqs, stream)
         entry.busy = True
-        self.inflight.append({"event": ev, "stream": stream, "entry": entry, "items": items,
-                              "keep": (rho, sigma), "out": out, "io": self._io_bytes(reqs)})
-        self.resident += self._io_bytes(reqs)
+        io = self._io_bytes(reqs)
+        self.inflight.append({"job": job, "stream": stream, "entry": entry, "items": items, "io": io})
+        self.resident += io
 
     def _complete(self):
         still = []
         for job in self.inflight:
-            if job["event"].query():
-                out = job["out"].numpy()
+            if self.backend.ready(job["job"]):
+                res = self.backend.results(job["job"])
                 now = time.perf_counter()
-                for i, (r, fut) in enumerate(job["items"]):
-                    self.latencies.append(now - r.submitted)
-                    fut.set_result(out[i])      # a view of the job's pinned buffer
+                # release the context, stream and buffers before waking the waiters, so a
+                # caller that resubmits at once finds them free
                 job["entry"].busy = False
                 self.free_streams.append(job["stream"])
                 self.resident -= job["io"]
+                for (r, fut), sig in zip(job["items"], res):
+                    self.latencies.append(now - r.submitted)
+                    fut.set_result(sig)
             else:
                 still.append(job)
         self.inflight = still
@@ -218,17 +287,25 @@ class StressServer:
                     continue                       # its context is on the GPU; try others
                 k = req.key()
                 group = [(r, f) for r, f in self.pending if r.key() == k][: self.max_batch]
-                need = self._io_bytes([r for r, _ in group])
-                if entry is None:
-                    # a new context's own footprint is known once it is built: make room for
-                    # the request's buffers, build (which accounts the context), then re-check
-                    if not self._make_room(need):
-                        continue
-                    entry = self._build_entry(req)
-                    if self.resident + need > self.budget and not self._make_room(need):
-                        continue
-                elif not self._make_room(need):
-                    continue
+                if entry is None and self._fit(group, None):
+                    # a new context's own footprint is known once it is built: room for the
+                    # buffers first, build (which accounts the context), then fit again below
+                    try:
+                        entry = self._build_entry(req)
+                    except Exception as ex:        # a context that cannot be built fails its requests only
+                        self._reject(k, ex)
+                        progressed = True
+                        break
+                if entry is not None:
+                    group = self._fit(group, k)
+                if entry is None or not group:
+                    if not self.inflight:
+                        # nothing else holds device memory: this request can never fit
+                        self._reject(k, MemoryError(
+                            f"stress request needs more than the {self.budget:.3g}-byte HBM budget"))
+                        progressed = True
+                        break
+                    continue                       # wait for work in flight to release memory
                 taken = {id(item[1]) for item in group}
                 self.pending = [x for x in self.pending if id(x[1]) not in taken]
                 self._launch(entry, group)
@@ -244,10 +321,13 @@ class StressServer:
                     except queue.Empty:
                         break
                     if msg[0] == "warm":
-                        _, req, done = msg
-                        if self._get_entry(req) is None:
-                            self._make_room(0)
-                            self._build_entry(req)
+                        _, req, done, err = msg
+                        try:
+                            if self._get_entry(req) is None:
+                                self._make_room(0)
+                                self._build_entry(req)
+                        except Exception as ex:
+                            err.append(ex)
                         done.set()
                     else:
                         self.pending.append(msg)

@@ -210,6 +210,7 @@ int make_plan(dds_ctx *ctx) {
   sh.fe = ctx->fe;
   sh.wz = 0;
   sh.zreg_g = 0;
+  sh.zfour = 0;
   sh.nb = 1;
   if (sh.pz <= 64 && sh.fe <= 4 && ctx->z_lanes >= 0) {
     // register-only z pass: E = pz / G registers per lane, E in {8, 16}
@@ -223,6 +224,17 @@ int make_plan(dds_ctx *ctx) {
     }
     if (ctx->z_lanes > 0)
       return fail(ctx, DDS_ERR_UNSUPPORTED, "z pass: %d lanes per column not available for pz %d", G, sh.pz);
+  }
+  // three-stage register z pass: padded z 128 or 256, at most 6 fields (default there)
+  const bool four_ok = (sh.pz == 128 || sh.pz == 256) && sh.fe <= 6 && sh.M % 8 == 0 && sh.py % 8 == 0;
+  if (ctx->z_lanes == -2 || (ctx->z_lanes == 0 && ctx->z_wz == 0 && four_ok)) {
+    if (!four_ok)
+      return fail(ctx, DDS_ERR_UNSUPPORTED, "z pass: the three-stage kernel needs pz 128 or 256 and <= 6 fields "
+                  "(pz %d, %d fields)", sh.pz, sh.fe);
+    sh.zfour = 1;
+    sh.wz = 8;
+    ctx->shape = sh;
+    return DDS_OK;
   }
   // shared-memory z pass: fe field lines and three component lines per column
   if (ctx->z_wz > 0) {                   // width fixed by the autotuner
@@ -413,8 +425,8 @@ int dds_set_option(dds_ctx *ctx, int key, double value) {
   if (!ctx) return DDS_ERR_INVALID_ARG;
   switch (key) {
     case DDS_OPT_Z_LANES:
-      if (!(value == -1 || value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
-        return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: z lanes must be -1, 0, 1, 2, 4 or 8");
+      if (!(value == -2 || value == -1 || value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
+        return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: z lanes must be -2, -1, 0, 1, 2, 4 or 8");
       ctx->z_lanes = (int)value;
       ctx->z_wz = 0;
       ctx->tuned = false;
@@ -481,6 +493,8 @@ int dds_autotune(dds_ctx *ctx, void *cuda_stream, float *best_ms) {
       if (base.pz % G == 0 && (E == 8 || E == 16) && base.M >= 32 / G) cand.push_back({G, 0});
     }
   }
+  if ((base.pz == 128 || base.pz == 256) && base.fe <= 6 && base.M % 8 == 0 && base.py % 8 == 0)
+    cand.push_back({-2, 0});
   for (int W : {4, 8, 16, 32, 64}) {
     if (W > base.M || base.py % W != 0 || (W * base.pz > 2048 && W > 8)) continue;
     const size_t fe = (size_t)std::max(base.fe, 1);
@@ -505,6 +519,7 @@ int dds_autotune(dds_ctx *ctx, void *cuda_stream, float *best_ms) {
     rc = make_plan(ctx);
     if (rc != DDS_OK) break;
     if (ctx->shape.zreg_g != (cand[i].first > 0 ? cand[i].first : 0)) continue;   // planner declined
+    if (ctx->shape.zfour != (cand[i].first == -2 ? 1 : 0)) continue;
     rc = alloc_buffers(ctx);
     if (rc != DDS_OK) break;
     const size_t vbytes = ctx->spectra_fp16 ? 2 : sizeof(float);

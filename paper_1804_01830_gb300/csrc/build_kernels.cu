@@ -302,7 +302,10 @@ __global__ void __launch_bounds__(256) k_cols_d(double2 *data, long os, long rs,
 // the fused z pass reads:
 //   shared-memory variant (zg = 0): kspec[tile][6][fe][pz][wz], tiles of wz columns;
 //   register variant (zg = G > 0):  kspec[warp tile][6][fe][lane][E], E = pz / G, warp
-//     tiles of 32/G columns, lane g * (32/G) + w holding kz = k1 + E bitrev_G(g), k1 < E.
+//     tiles of 32/G columns, lane g * (32/G) + w holding kz = k1 + E bitrev_G(g), k1 < E;
+//   three-stage variant (zg = -1, pz = 8 R1, tiles of wz = 8 columns): per (tile, c)
+//     16-byte chunks [j][thread t = k1 wz + w], the value of (e, kz = k1 + R1 k2) at
+//     position (8 e + k2) % V of chunk j = (8 e + k2) / V, V values per chunk.
 // Main tiles cover (ky, kx < M) row by row; the Nyquist tiles (kx = M) follow.
 __device__ __forceinline__ void store_val(float *p, double v) { *p = (float)v; }
 __device__ __forceinline__ void store_val(__half *p, double v) { *p = __float2half_rn((float)v); }
@@ -326,7 +329,7 @@ __global__ void k_store_scale(const unsigned long long *amax, double scale, floa
 template <typename OT>
 __global__ void k_extract(const double2 *spec, int M, int py, int pz, int wz, int zg, int fe, int e, int c,
                           double scale, const unsigned long long *amax, OT *kspec) {
-  const int cw = zg > 0 ? 32 / zg : wz;                  // columns per tile
+  const int cw = zg > 0 ? 32 / zg : wz;                  // columns per tile (zg < 0: wz)
   const int E = zg > 0 ? pz / zg : 0;                     // registers per lane
   const long per_tile = zg > 0 ? 32L * E : (long)pz * wz;
   const long tiles_main = (long)py * (M / cw);
@@ -336,7 +339,14 @@ __global__ void k_extract(const double2 *spec, int M, int py, int pz, int wz, in
   const long tau = idx / per_tile;
   const int r = (int)(idx % per_tile);
   int kz, w;
-  if (zg > 0) {
+  long dst = ((tau * 6 + c) * fe + e) * per_tile + r;
+  if (zg < 0) {
+    constexpr int V = 16 / (int)sizeof(OT);
+    const int t = r / 8, k2 = r % 8, R1 = pz / 8, q = 8 * e + k2;
+    w = t % wz;
+    kz = t / wz + R1 * k2;
+    dst = (tau * 6 + c) * fe * per_tile + ((long)(q / V) * (R1 * wz) + t) * V + q % V;
+  } else if (zg > 0) {
     const int lane = r / E, k1 = r % E, g = lane / cw;
     const int gb = zg == 4 ? (((g & 1) << 1) | (g >> 1))
                  : zg == 8 ? (((g & 1) << 2) | (g & 2) | (g >> 2)) : g;
@@ -359,7 +369,7 @@ __global__ void k_extract(const double2 *spec, int M, int py, int pz, int wz, in
     const double m = __longlong_as_double((long long)*amax) * scale;
     if (m > 0.0) v /= m;
   }
-  store_val(&kspec[((tau * 6 + c) * fe + e) * per_tile + r], v);
+  store_val(&kspec[dst], v);
 }
 
 template <int M>
@@ -514,12 +524,14 @@ int build_spectra(dds_ctx *ctx, cudaStream_t s) {
             k_absmax_imag<<<1024, 256, 0, s>>>(spec, nspec, d_amax);
             k_store_scale<<<1, 1, 0, s>>>(d_amax, scale, ctx->kscale, c * sh.fe + e);
             k_extract<__half><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-                spec, M, py, pz, sh.wz, sh.zreg_g, sh.fe, e, c, scale, d_amax, static_cast<__half *>(ctx->kspec));
+                spec, M, py, pz, sh.wz, sh.zfour ? -1 : sh.zreg_g, sh.fe, e, c, scale, d_amax,
+                static_cast<__half *>(ctx->kspec));
             err = cudaGetLastError();
           }
         } else {
           k_extract<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-              spec, M, py, pz, sh.wz, sh.zreg_g, sh.fe, e, c, scale, nullptr, static_cast<float *>(ctx->kspec));
+              spec, M, py, pz, sh.wz, sh.zfour ? -1 : sh.zreg_g, sh.fe, e, c, scale, nullptr,
+              static_cast<float *>(ctx->kspec));
           err = cudaGetLastError();
         }
       }

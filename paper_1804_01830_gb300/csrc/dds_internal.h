@@ -36,6 +36,7 @@ struct Shape {
   int fin, fe;        // input families, effective fields
   int wz;             // columns per tile of the fused z pass (shared-memory variant)
   int zreg_g;         // > 0: register-only z pass, pz = 16 * zreg_g, zreg_g lanes per column
+  int zfour;          // 1: three-stage register z pass (pz 128 or 256, tiles of 8 columns)
   int nb;             // density sets evaluated together (batch); fields are [b][e], outputs [b][c]
 };
 

@@ -1,0 +1,194 @@
+// Fused z pass for padded z sizes 128 and 256 (PZ = 8 R1), in three register stages
+// of the four-step factorisation: forward n = n2 + 8 n1, k = k1 + R1 k2; inverse
+// k = k1 + R1 k2, n = a + 8 b.  A CTA takes 8 adjacent columns with PZ threads:
+//   stage 1  thread (field e, n2, column w) loads rows n2 + 8 n1 < nz straight from
+//            global memory (64-byte row segments), runs the R1-point DFT of the
+//            half-zero input (two R1/2-point DFTs), twiddles by W_PZ^(n2 k1) and
+//            writes T[e][k1][n2][w];
+//   stage 2  thread (k1, w) reads its 8 values of every field, runs the 8-point DFTs
+//            and keeps rho^_e(k1 + R1 k2) of all fields in registers; for each
+//            component it loads its kernel spectra straight from global memory (laid
+//            out per thread in 16-byte chunks), contracts (Eq. 10 in Fourier space),
+//            runs the inverse 8-point DFT over k2, twiddles by conj W_PZ^(a k1) and
+//            writes Y[c][a][k1][w] into the space of T;
+//   stage 3  thread (c, a, w) reads the R1 values of k1, runs the inverse R1-point DFT
+//            for the outputs b < R1/2 only (rows a + 8 b < nz <= PZ/2) and stores them.
+// Shared memory is written and read once per stage; row strides of 8 (mod 16) values
+// keep every stage's half-warp accesses free of bank conflicts.
+#pragma once
+#include "stress_common.cuh"
+
+namespace dds {
+namespace zp {
+
+constexpr int ZF_W = 8;   // columns per tile
+
+template <int PZ> struct ZF {
+  static constexpr int R2 = 8, R1 = PZ / 8, NT = PZ;
+  static constexpr int SK = R2 * ZF_W + 8;   // T row (e, k1): 8 n2 x 8 columns
+  static constexpr int SY = R1 * ZF_W + 8;   // Y row (c, a): R1 k1 x 8 columns
+  static_assert(R1 == 16 || R1 == 32, "padded z size 128 or 256");
+};
+
+// shared memory of the kernel, in float2 values: T, or Y in the same space
+template <int PZ> __host__ __device__ constexpr int zf_smem(int fe) {
+  return fe * ZF<PZ>::R1 * ZF<PZ>::SK > 6 * ZF<PZ>::R2 * ZF<PZ>::SY ? fe * ZF<PZ>::R1 * ZF<PZ>::SK
+                                                                    : 6 * ZF<PZ>::R2 * ZF<PZ>::SY;
+}
+
+// The 8 kernel-spectrum values k2 = 0..7 of field e for the calling thread, times s.
+// Layout of one (tile, component): 16-byte chunks [j][thread], value (e, k2) in chunk
+// j = (8 e + k2) / (values per chunk).
+__device__ __forceinline__ void zf_spectra8(const float *kc, int e, int t, int nthreads, float s, float (&g)[8]) {
+  const float4 *p = reinterpret_cast<const float4 *>(kc);
+  const float4 a = __ldg(p + (long)(2 * e) * nthreads + t), b = __ldg(p + (long)(2 * e + 1) * nthreads + t);
+  g[0] = a.x * s; g[1] = a.y * s; g[2] = a.z * s; g[3] = a.w * s;
+  g[4] = b.x * s; g[5] = b.y * s; g[6] = b.z * s; g[7] = b.w * s;
+}
+__device__ __forceinline__ void zf_spectra8(const __half *kc, int e, int t, int nthreads, float s, float (&g)[8]) {
+  const uint4 q = __ldg(reinterpret_cast<const uint4 *>(kc) + (long)e * nthreads + t);
+  const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[i]));
+    g[2 * i] = f.x * s;
+    g[2 * i + 1] = f.y * s;
+  }
+}
+
+template <int PZ, int FE, typename GT>
+__global__ void __launch_bounds__(PZ, 512 / PZ) k_zfour(Shape sh, const float2 *in_main, const float2 *in_nyq,
+                                                         const GT *kspec, const float *kscale, float2 *out_main,
+                                                         float2 *out_nyq, const float2 *tw) {
+  constexpr int R1 = ZF<PZ>::R1, R2 = ZF<PZ>::R2, W = ZF_W, NT = ZF<PZ>::NT;
+  constexpr int SK = ZF<PZ>::SK, SY = ZF<PZ>::SY, H = R1 / 2;
+  extern __shared__ __align__(16) float2 zsm[];
+  const int tid = threadIdx.x;
+  const int M = sh.M, py = sh.py, nz = sh.nz;
+  const long ktiles = M / W, tiles_main = (long)py * ktiles;
+  // Consecutive blocks take the same column tile for the density sets of a batch,
+  // so the tile's kernel spectra come from HBM once and from L2 for the others.
+  const long tau = blockIdx.x / sh.nb;
+  const int bset = (int)(blockIdx.x - tau * sh.nb);
+  in_main += bset * ((long)FE * nz * py * M);
+  in_nyq += bset * ((long)FE * py * nz);
+  out_main += bset * (6L * nz * py * M);
+  out_nyq += bset * (6L * py * nz);
+  const bool nyq = tau >= tiles_main;
+  long ky = 0, kx0 = 0, ky0 = 0;
+  if (!nyq) {
+    ky = tau / ktiles;
+    kx0 = (tau - ky * ktiles) * W;
+  } else {
+    ky0 = (tau - tiles_main) * W;
+  }
+  const float2 *twP = tw + tw_offset(PZ);
+
+  // stage 1: forward R1-point DFTs over n1 of the rows n2 + 8 n1 (n1 < R1/2 non-zero)
+  for (int item = tid; item < FE * R2 * W; item += NT) {
+    const int e = item / (R2 * W), r = item - e * (R2 * W), n2 = r / W, w = r - n2 * W;
+    float2 ev[H], od[H];
+#pragma unroll
+    for (int n1 = 0; n1 < H; ++n1) {
+      const int z = n2 + R2 * n1;
+      ev[n1] = make_float2(0.f, 0.f);
+      if (z < nz)
+        ev[n1] = !nyq ? __ldg(in_main + (((long)e * nz + z) * py + ky) * M + kx0 + w)
+                      : __ldg(in_nyq + ((long)e * py + ky0 + w) * nz + z);
+    }
+#pragma unroll
+    for (int n1 = 0; n1 < H; ++n1) od[n1] = rot_const<false>(ev[n1], n1, R1);
+    dft_reg<H, false>(ev);                    // outputs k1 = 2 j
+    dft_reg<H, false>(od);                    // outputs k1 = 2 j + 1
+    float2 *T = zsm + (long)e * R1 * SK + n2 * W + w;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      T[(2 * j) * SK] = j == 0 ? ev[0] : cmul_tw<false>(ev[j], __ldg(twP + n2 * 2 * j));
+      T[(2 * j + 1) * SK] = cmul_tw<false>(od[j], __ldg(twP + n2 * (2 * j + 1)));
+    }
+  }
+  __syncthreads();
+
+  // stage 2: forward 8-point DFTs over n2, contraction, inverse 8-point DFTs over k2
+  const int k1 = tid / W, w = tid - k1 * W;
+  float2 f[FE][R2];
+#pragma unroll
+  for (int e = 0; e < FE; ++e) {
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) f[e][n2] = zsm[((long)e * R1 + k1) * SK + n2 * W + w];
+    dft_reg<R2, false>(f[e]);
+  }
+  __syncthreads();                            // T is read: Y takes its space
+  const GT *ks = kspec + tau * 6L * FE * PZ * W;
+#pragma unroll 1
+  for (int c = 0; c < 6; ++c) {
+    const GT *kc = ks + (long)c * FE * PZ * W;
+    float2 s[R2];
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) s[k2] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int e = 0; e < FE; ++e) {
+      float g[8];
+      zf_spectra8(kc, e, tid, NT, kscale != nullptr ? __ldg(kscale + c * FE + e) : 1.0f, g);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) s[k2] = cmadd_i(s[k2], g[k2], f[e][k2]);
+    }
+    dft_reg<R2, true>(s);                     // index a of n = a + 8 b
+    float2 *Y = zsm + (long)c * R2 * SY + k1 * W + w;
+    Y[0] = s[0];
+#pragma unroll
+    for (int a = 1; a < R2; ++a) Y[a * SY] = cmul_tw<true>(s[a], __ldg(twP + a * k1));
+  }
+  __syncthreads();
+
+  // stage 3: inverse R1-point DFTs over k1, outputs b < R1/2: x(b) = E(b) + W_R1^-b O(b)
+  for (int item = tid; item < 6 * R2 * W; item += NT) {
+    const int c = item / (R2 * W), r = item - c * (R2 * W), a = r / W, wc = r - a * W;
+    const float2 *Y = zsm + ((long)c * R2 + a) * SY + wc;
+    float2 ev[H], od[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      ev[j] = Y[(2 * j) * W];
+      od[j] = Y[(2 * j + 1) * W];
+    }
+    dft_reg<H, true>(ev);
+    dft_reg<H, true>(od);
+#pragma unroll
+    for (int b = 0; b < H; ++b) {
+      const int z = a + R2 * b;
+      if (z < nz) {
+        const float2 v = cadd(ev[b], rot_const<true>(od[b], b, R1));
+        if (!nyq) out_main[(((long)c * nz + z) * py + ky) * M + kx0 + wc] = v;
+        else out_nyq[((long)c * py + ky0 + wc) * nz + z] = v;
+      }
+    }
+  }
+}
+
+template <int PZ, int FE, typename GT>
+cudaError_t launch_zfour(const Shape &sh, const float2 *im, const float2 *in, const GT *ks, const float *ksc,
+                         float2 *om, float2 *on, const float2 *tw, cudaStream_t s) {
+  const size_t smem = sizeof(float2) * (size_t)zf_smem<PZ>(FE);
+  const long tiles = ((long)sh.py * (sh.M / ZF_W) + sh.py / ZF_W) * sh.nb;
+  cudaError_t err = prep(k_zfour<PZ, FE, GT>, smem);
+  if (err != cudaSuccess) return err;
+  k_zfour<PZ, FE, GT><<<(unsigned)tiles, PZ, smem, s>>>(sh, im, in, ks, ksc, om, on, tw);
+  return cudaGetLastError();
+}
+
+template <int PZ, typename GT>
+cudaError_t dispatch_zfour_fe(const Shape &sh, const float2 *im, const float2 *in, const GT *ks, const float *ksc,
+                              float2 *om, float2 *on, const float2 *tw, cudaStream_t s) {
+  switch (sh.fe) {
+    case 1: return launch_zfour<PZ, 1, GT>(sh, im, in, ks, ksc, om, on, tw, s);
+    case 2: return launch_zfour<PZ, 2, GT>(sh, im, in, ks, ksc, om, on, tw, s);
+    case 3: return launch_zfour<PZ, 3, GT>(sh, im, in, ks, ksc, om, on, tw, s);
+    case 4: return launch_zfour<PZ, 4, GT>(sh, im, in, ks, ksc, om, on, tw, s);
+    case 5: return launch_zfour<PZ, 5, GT>(sh, im, in, ks, ksc, om, on, tw, s);
+    case 6: return launch_zfour<PZ, 6, GT>(sh, im, in, ks, ksc, om, on, tw, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace zp
+}  // namespace dds

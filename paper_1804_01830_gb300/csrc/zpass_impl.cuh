@@ -6,6 +6,7 @@
 // (component, field); arithmetic is FP32 either way.
 #pragma once
 #include "stress_common.cuh"
+#include "zfour.cuh"
 
 namespace dds {
 namespace zp {
@@ -431,6 +432,11 @@ cudaError_t dispatch_zreg_fe(const Shape &sh, const float2 *im, const float2 *in
 template <typename GT>
 cudaError_t dispatch_z_typed(const Shape &sh, const float2 *im, const float2 *in, const GT *ks, const float *ksc,
                              float2 *om, float2 *on, const float2 *tw, cudaStream_t s) {
+  if (sh.zfour) {
+    if (sh.pz == 128) return dispatch_zfour_fe<128, GT>(sh, im, in, ks, ksc, om, on, tw, s);
+    if (sh.pz == 256) return dispatch_zfour_fe<256, GT>(sh, im, in, ks, ksc, om, on, tw, s);
+    return cudaErrorInvalidValue;
+  }
   if (sh.zreg_g > 0) {
     switch (sh.pz * 16 + sh.zreg_g) {   // (pz, lanes per column) -> E = pz / G registers
       case 16 * 16 + 1: return dispatch_zreg_fe<16, 1, GT>(sh, im, in, ks, ksc, om, on, tw, s);

@@ -226,13 +226,14 @@ int make_plan(dds_ctx *ctx) {
       return fail(ctx, DDS_ERR_UNSUPPORTED, "z pass: %d lanes per column not available for pz %d", G, sh.pz);
   }
   // three-stage register z pass: padded z 128 or 256, at most 6 fields (default there)
-  const bool four_ok = (sh.pz == 128 || sh.pz == 256) && sh.fe <= 6 && sh.M % 8 == 0 && sh.py % 8 == 0;
+  const int fw = zfour_width(sh.pz);
+  const bool four_ok = (sh.pz == 128 || sh.pz == 256) && sh.fe <= 6 && sh.M % fw == 0 && sh.py % fw == 0;
   if (ctx->z_lanes == -2 || (ctx->z_lanes == 0 && ctx->z_wz == 0 && four_ok)) {
     if (!four_ok)
       return fail(ctx, DDS_ERR_UNSUPPORTED, "z pass: the three-stage kernel needs pz 128 or 256 and <= 6 fields "
                   "(pz %d, %d fields)", sh.pz, sh.fe);
     sh.zfour = 1;
-    sh.wz = 8;
+    sh.wz = fw;
     ctx->shape = sh;
     return DDS_OK;
   }
@@ -493,7 +494,8 @@ int dds_autotune(dds_ctx *ctx, void *cuda_stream, float *best_ms) {
       if (base.pz % G == 0 && (E == 8 || E == 16) && base.M >= 32 / G) cand.push_back({G, 0});
     }
   }
-  if ((base.pz == 128 || base.pz == 256) && base.fe <= 6 && base.M % 8 == 0 && base.py % 8 == 0)
+  if ((base.pz == 128 || base.pz == 256) && base.fe <= 6 && base.M % zfour_width(base.pz) == 0 &&
+      base.py % zfour_width(base.pz) == 0)
     cand.push_back({-2, 0});
   for (int W : {4, 8, 16, 32, 64}) {
     if (W > base.M || base.py % W != 0 || (W * base.pz > 2048 && W > 8)) continue;

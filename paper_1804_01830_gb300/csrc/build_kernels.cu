@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(256) k_cols_d(double2 *data, long os, long rs,
 //   shared-memory variant (zg = 0): kspec[tile][6][fe][pz][wz], tiles of wz columns;
 //   register variant (zg = G > 0):  kspec[warp tile][6][fe][lane][E], E = pz / G, warp
 //     tiles of 32/G columns, lane g * (32/G) + w holding kz = k1 + E bitrev_G(g), k1 < E;
-//   three-stage variant (zg = -1, pz = 8 R1, tiles of wz = 8 columns): per (tile, c)
+//   three-stage variant (zg = -1, pz = 8 R1, tiles of wz columns): per (tile, c)
 //     16-byte chunks [j][thread t = k1 wz + w], the value of (e, kz = k1 + R1 k2) at
 //     position (8 e + k2) % V of chunk j = (8 e + k2) / V, V values per chunk.
 // Main tiles cover (ky, kx < M) row by row; the Nyquist tiles (kx = M) follow.

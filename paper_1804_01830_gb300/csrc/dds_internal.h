@@ -36,9 +36,12 @@ struct Shape {
   int fin, fe;        // input families, effective fields
   int wz;             // columns per tile of the fused z pass (shared-memory variant)
   int zreg_g;         // > 0: register-only z pass, pz = 16 * zreg_g, zreg_g lanes per column
-  int zfour;          // 1: three-stage register z pass (pz 128 or 256, tiles of 8 columns)
+  int zfour;          // 1: three-stage register z pass (pz 128 or 256, wz = zfour_width(pz))
   int nb;             // density sets evaluated together (batch); fields are [b][e], outputs [b][c]
 };
+
+// Columns per tile of the three-stage z pass (Shape::zfour) for padded z size pz.
+__host__ __device__ constexpr int zfour_width(int pz) { return pz >= 256 ? 8 : 16; }
 
 // FP64 description of a box coefficient (Eq. 9b times the cell volume).
 struct CoefGeom {

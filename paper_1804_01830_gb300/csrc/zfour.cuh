@@ -1,8 +1,9 @@
 // Fused z pass for padded z sizes 128 and 256 (PZ = 8 R1), in three register stages
 // of the four-step factorisation: forward n = n2 + 8 n1, k = k1 + R1 k2; inverse
-// k = k1 + R1 k2, n = a + 8 b.  A CTA takes 8 adjacent columns with PZ threads:
+// k = k1 + R1 k2, n = a + 8 b.  A CTA takes W adjacent columns (16 for PZ 128: rows of
+// 128 bytes; 8 for PZ 256, so that two CTAs fit an SM) with R1 W threads:
 //   stage 1  thread (field e, n2, column w) loads rows n2 + 8 n1 < nz straight from
-//            global memory (64-byte row segments), runs the R1-point DFT of the
+//            global memory (row segments of W complex values), runs the R1-point DFT of the
 //            half-zero input (two R1/2-point DFTs), twiddles by W_PZ^(n2 k1) and
 //            writes T[e][k1][n2][w];
 //   stage 2  thread (k1, w) reads its 8 values of every field, runs the 8-point DFTs
@@ -13,20 +14,19 @@
 //            writes Y[c][a][k1][w] into the space of T;
 //   stage 3  thread (c, a, w) reads the R1 values of k1, runs the inverse R1-point DFT
 //            for the outputs b < R1/2 only (rows a + 8 b < nz <= PZ/2) and stores them.
-// Shared memory is written and read once per stage; row strides of 8 (mod 16) values
-// keep every stage's half-warp accesses free of bank conflicts.
+// Shared memory is written and read once per stage; row strides of 9 W values (T) and
+// (R1 + 1) W values (Y) keep every stage's half-warp accesses free of bank conflicts.
 #pragma once
 #include "stress_common.cuh"
 
 namespace dds {
 namespace zp {
 
-constexpr int ZF_W = 8;   // columns per tile
-
 template <int PZ> struct ZF {
-  static constexpr int R2 = 8, R1 = PZ / 8, NT = PZ;
-  static constexpr int SK = R2 * ZF_W + 8;   // T row (e, k1): 8 n2 x 8 columns
-  static constexpr int SY = R1 * ZF_W + 8;   // Y row (c, a): R1 k1 x 8 columns
+  static constexpr int W = zfour_width(PZ);   // columns per tile
+  static constexpr int R2 = 8, R1 = PZ / 8, NT = R1 * W;
+  static constexpr int SK = (R2 + 1) * W;     // T row (e, k1): 8 n2 x W columns + W
+  static constexpr int SY = (R1 + 1) * W;     // Y row (c, a): R1 k1 x W columns + W
   static_assert(R1 == 16 || R1 == 32, "padded z size 128 or 256");
 };
 
@@ -36,31 +36,52 @@ template <int PZ> __host__ __device__ constexpr int zf_smem(int fe) {
                                                                     : 6 * ZF<PZ>::R2 * ZF<PZ>::SY;
 }
 
-// The 8 kernel-spectrum values k2 = 0..7 of field e for the calling thread, times s.
-// Layout of one (tile, component): 16-byte chunks [j][thread], value (e, k2) in chunk
+// The kernel-spectrum values (e, k2 = 0..7), e < FE, of one component for the calling
+// thread, fields e0 .. e0 + FE - 1, held raw in registers (FP32, or FP16 converted and
+// scaled at use).  Layout of
+// one (tile, component): 16-byte chunks [j][thread], value (e, k2) in chunk
 // j = (8 e + k2) / (values per chunk).
-__device__ __forceinline__ void zf_spectra8(const float *kc, int e, int t, int nthreads, float s, float (&g)[8]) {
-  const float4 *p = reinterpret_cast<const float4 *>(kc);
-  const float4 a = __ldg(p + (long)(2 * e) * nthreads + t), b = __ldg(p + (long)(2 * e + 1) * nthreads + t);
-  g[0] = a.x * s; g[1] = a.y * s; g[2] = a.z * s; g[3] = a.w * s;
-  g[4] = b.x * s; g[5] = b.y * s; g[6] = b.z * s; g[7] = b.w * s;
-}
-__device__ __forceinline__ void zf_spectra8(const __half *kc, int e, int t, int nthreads, float s, float (&g)[8]) {
-  const uint4 q = __ldg(reinterpret_cast<const uint4 *>(kc) + (long)e * nthreads + t);
-  const unsigned w[4] = {q.x, q.y, q.z, q.w};
+template <typename GT, int FE> struct ZRaw;
+template <int FE> struct ZRaw<float, FE> {
+  float4 v[FE][2];
+  __device__ __forceinline__ void load(const float *kc, int e0, int t, int nthreads) {
+    const float4 *p = reinterpret_cast<const float4 *>(kc);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[i]));
-    g[2 * i] = f.x * s;
-    g[2 * i + 1] = f.y * s;
+    for (int e = 0; e < FE; ++e) {
+      v[e][0] = __ldg(p + (long)(2 * (e0 + e)) * nthreads + t);
+      v[e][1] = __ldg(p + (long)(2 * (e0 + e) + 1) * nthreads + t);
+    }
   }
+  __device__ __forceinline__ float get(int e, int k2, float) const {
+    const float4 q = v[e][k2 / 4];
+    return (k2 % 4 == 0) ? q.x : (k2 % 4 == 1) ? q.y : (k2 % 4 == 2) ? q.z : q.w;
+  }
+};
+template <int FE> struct ZRaw<__half, FE> {
+  uint4 v[FE];
+  __device__ __forceinline__ void load(const __half *kc, int e0, int t, int nthreads) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(kc);
+#pragma unroll
+    for (int e = 0; e < FE; ++e) v[e] = __ldg(p + (long)(e0 + e) * nthreads + t);
+  }
+  __device__ __forceinline__ float get(int e, int k2, float s) const {
+    const uint4 q = v[e];
+    const unsigned w = (k2 / 2 == 0) ? q.x : (k2 / 2 == 1) ? q.y : (k2 / 2 == 2) ? q.z : q.w;
+    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+    return ((k2 % 2) ? f.y : f.x) * s;
+  }
+};
+
+// Prefetch of [p, p + bytes) into L2 by the bulk-copy unit; p and bytes multiples of 16.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
 template <int PZ, int FE, typename GT>
-__global__ void __launch_bounds__(PZ, 512 / PZ) k_zfour(Shape sh, const float2 *in_main, const float2 *in_nyq,
+__global__ void __launch_bounds__(ZF<PZ>::NT, 512 / ZF<PZ>::NT) k_zfour(Shape sh, const float2 *in_main, const float2 *in_nyq,
                                                          const GT *kspec, const float *kscale, float2 *out_main,
                                                          float2 *out_nyq, const float2 *tw) {
-  constexpr int R1 = ZF<PZ>::R1, R2 = ZF<PZ>::R2, W = ZF_W, NT = ZF<PZ>::NT;
+  constexpr int R1 = ZF<PZ>::R1, R2 = ZF<PZ>::R2, W = ZF<PZ>::W, NT = ZF<PZ>::NT;
   constexpr int SK = ZF<PZ>::SK, SY = ZF<PZ>::SY, H = R1 / 2;
   extern __shared__ __align__(16) float2 zsm[];
   const int tid = threadIdx.x;
@@ -83,6 +104,14 @@ __global__ void __launch_bounds__(PZ, 512 / PZ) k_zfour(Shape sh, const float2 *
     ky0 = (tau - tiles_main) * W;
   }
   const float2 *twP = tw + tw_offset(PZ);
+  // the tile's kernel spectra (6 FE PZ W values, contiguous) head for L2 now, so the
+  // per-component loads of stage 2 find them there
+  const GT *ks = kspec + tau * 6L * FE * PZ * W;
+  {
+    constexpr unsigned BYTES = 6u * FE * PZ * W * sizeof(GT), CH = 8192, NCH = (BYTES + CH - 1) / CH;
+    static_assert(BYTES % 16 == 0 && NCH <= NT, "prefetch chunks");
+    if (tid < (int)NCH) prefetch_l2_bulk(reinterpret_cast<const char *>(ks) + tid * CH, min(CH, BYTES - tid * CH));
+  }
 
   // stage 1: forward R1-point DFTs over n1 of the rows n2 + 8 n1 (n1 < R1/2 non-zero)
   for (int item = tid; item < FE * R2 * W; item += NT) {
@@ -109,8 +138,13 @@ __global__ void __launch_bounds__(PZ, 512 / PZ) k_zfour(Shape sh, const float2 *
   }
   __syncthreads();
 
-  // stage 2: forward 8-point DFTs over n2, contraction, inverse 8-point DFTs over k2
+  // stage 2: forward 8-point DFTs over n2, contraction, inverse 8-point DFTs over k2;
+  // the spectra of the next component (of its first PF fields, as registers allow) load
+  // while the current one is inverted and stored
+  constexpr int PF = FE <= 4 ? FE : (FE == 5 ? 2 : 1);
   const int k1 = tid / W, w = tid - k1 * W;
+  ZRaw<GT, PF> gr;
+  gr.load(ks, 0, tid, NT);
   float2 f[FE][R2];
 #pragma unroll
   for (int e = 0; e < FE; ++e) {
@@ -119,7 +153,6 @@ __global__ void __launch_bounds__(PZ, 512 / PZ) k_zfour(Shape sh, const float2 *
     dft_reg<R2, false>(f[e]);
   }
   __syncthreads();                            // T is read: Y takes its space
-  const GT *ks = kspec + tau * 6L * FE * PZ * W;
 #pragma unroll 1
   for (int c = 0; c < 6; ++c) {
     const GT *kc = ks + (long)c * FE * PZ * W;
@@ -128,11 +161,18 @@ __global__ void __launch_bounds__(PZ, 512 / PZ) k_zfour(Shape sh, const float2 *
     for (int k2 = 0; k2 < R2; ++k2) s[k2] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int e = 0; e < FE; ++e) {
-      float g[8];
-      zf_spectra8(kc, e, tid, NT, kscale != nullptr ? __ldg(kscale + c * FE + e) : 1.0f, g);
+      const float sc = kscale != nullptr ? __ldg(kscale + c * FE + e) : 1.0f;
+      if (e < PF) {
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) s[k2] = cmadd_i(s[k2], g[k2], f[e][k2]);
+        for (int k2 = 0; k2 < R2; ++k2) s[k2] = cmadd_i(s[k2], gr.get(e, k2, sc), f[e][k2]);
+      } else {
+        ZRaw<GT, 1> late;
+        late.load(kc, e, tid, NT);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) s[k2] = cmadd_i(s[k2], late.get(0, k2, sc), f[e][k2]);
+      }
     }
+    if (c < 5) gr.load(kc + (long)FE * PZ * W, 0, tid, NT);
     dft_reg<R2, true>(s);                     // index a of n = a + 8 b
     float2 *Y = zsm + (long)c * R2 * SY + k1 * W + w;
     Y[0] = s[0];
@@ -169,10 +209,12 @@ template <int PZ, int FE, typename GT>
 cudaError_t launch_zfour(const Shape &sh, const float2 *im, const float2 *in, const GT *ks, const float *ksc,
                          float2 *om, float2 *on, const float2 *tw, cudaStream_t s) {
   const size_t smem = sizeof(float2) * (size_t)zf_smem<PZ>(FE);
-  const long tiles = ((long)sh.py * (sh.M / ZF_W) + sh.py / ZF_W) * sh.nb;
+  constexpr int W = ZF<PZ>::W;
+  if (sh.wz != W) return cudaErrorInvalidValue;
+  const long tiles = ((long)sh.py * (sh.M / W) + sh.py / W) * sh.nb;
   cudaError_t err = prep(k_zfour<PZ, FE, GT>, smem);
   if (err != cudaSuccess) return err;
-  k_zfour<PZ, FE, GT><<<(unsigned)tiles, PZ, smem, s>>>(sh, im, in, ks, ksc, om, on, tw);
+  k_zfour<PZ, FE, GT><<<(unsigned)tiles, ZF<PZ>::NT, smem, s>>>(sh, im, in, ks, ksc, om, on, tw);
   return cudaGetLastError();
 }
 

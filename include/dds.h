@@ -61,10 +61,14 @@ enum {
                               (Sec. 2.3 "several nearest-neighbour shells"); default 3;
                               0 disables subdivision.  Invalidates built kernels. */
   DDS_OPT_Z_LANES = 2,     /* schedule of the fused z pass: 0 = automatic (default);
-                              -1 = shared-memory tiles; 1, 2, 4, 8 = register-only kernel
+                              -1 = shared-memory tiles; -2 = three-stage register kernel
+                              (padded z size 128 or 256, <= 6 combined fields; the
+                              automatic choice there); 1, 2, 4, 8 = register-only kernel
                               with that many lanes per (kx, ky) column (needs padded
                               z size <= 64 and <= 4 combined fields).  Same result up to
-                              rounding; a tuning knob.  Invalidates built kernels. */
+                              rounding; a tuning knob.  A schedule the grid cannot take
+                              fails dds_build_kernels with DDS_ERR_UNSUPPORTED.
+                              Invalidates built kernels. */
   DDS_OPT_PBC_SHELLS = 4,  /* in-plane periodic boundary conditions (Sec. 4): n > 0 makes
                               every coefficient the sum over the replicas of the source
                               cell, r_i + (k Lx, l Ly, 0) with |k|, |l| <= n (Eq. 12-13;

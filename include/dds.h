@@ -49,7 +49,7 @@ enum {
   DDS_ERR_OOM = -3,           /* device allocation failed                          */
   DDS_ERR_CUDA = -4,          /* a CUDA runtime call or kernel launch failed       */
   DDS_ERR_TIMEOUT = -5,       /* a bounded device wait gave up                     */
-  DDS_ERR_UNSUPPORTED = -6    /* valid request outside this build's limits         */
+  DDS_ERR_UNSUPPORTED = -6    /* valid request outside the library's limits        */
 };
 
 /* Density element types accepted by dds_stress. */
@@ -83,7 +83,7 @@ enum {
                               kernels. */
 };
 
-/* Limits of this build. */
+/* Compile-time limits of the library. */
 #define DDS_MAX_NXY 512        /* nx, ny <= 512 (zero-padded FFT sizes <= 1024)      */
 #define DDS_MAX_NZ 256         /* nz <= 256 (zero-padded FFT size <= 512)            */
 #define DDS_MAX_FAMILIES 64    /* families per context                               */

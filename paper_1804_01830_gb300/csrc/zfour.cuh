@@ -36,11 +36,10 @@ template <int PZ> __host__ __device__ constexpr int zf_smem(int fe) {
                                                                     : 6 * ZF<PZ>::R2 * ZF<PZ>::SY;
 }
 
-// The kernel-spectrum values (e, k2 = 0..7), e < FE, of one component for the calling
-// thread, fields e0 .. e0 + FE - 1, held raw in registers (FP32, or FP16 converted and
-// scaled at use).  Layout of
-// one (tile, component): 16-byte chunks [j][thread], value (e, k2) in chunk
-// j = (8 e + k2) / (values per chunk).
+// The kernel-spectrum values (e, k2 = 0..7) of fields e = e0 .. e0 + FE - 1 of one
+// component for the calling thread, held raw in registers (FP32, or FP16 converted and
+// scaled at use).  Layout of one (tile, component): 16-byte chunks [j][thread], value
+// (e, k2) in chunk j = (8 e + k2) / (values per chunk).
 template <typename GT, int FE> struct ZRaw;
 template <int FE> struct ZRaw<float, FE> {
   float4 v[FE][2];

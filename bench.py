@@ -370,8 +370,8 @@ def sweep_benchmark(device: int, n_real: int = 64, reps: int = 5, oracle_targets
     one context per grid with an autotuned z schedule, all realisations of a grid in one
     batch, and the whole sweep captured as one CUDA graph (FP32 densities, and again with
     BF16 densities).  Time per sweep over `reps` graph launches (CUDA events); the same
-    realisations evaluated one by one for comparison; BF16 against FP32; one realisation
-    against the FP64 oracle on sampled target cells."""
+    realisations evaluated one by one for comparison; BF16 against FP32; the FP64 oracle
+    timed on sampled target cells of one realisation as the CPU baseline."""
     import numpy as np
     import torch
     import oracle
@@ -433,21 +433,17 @@ def sweep_benchmark(device: int, n_real: int = 64, reps: int = 5, oracle_targets
                    b.double().reshape(b.shape[0], 6, -1).norm(dim=2).clamp_min(1e-30)).max())
             for a, b in zip(g16.sigma, g32.sigma))
     out["bf16_rel_l2_vs_fp32_max"] = d
-    # realisation 0 against the FP64 oracle on sampled targets
+    # CPU baseline of the sweep: the FP64 oracle's direct sum on sampled target cells of
+    # realisation 0 (its parity with the GPU is a test, not part of the benchmark)
     r0 = 0
     g0, D0 = W.sweep_spec(r0)
-    k0 = sorted(groups).index((g0.nx, g0.ny, g0.nz))
-    i0 = [r for r, _, _ in groups[(g0.nx, g0.ny, g0.nz)]].index(r0)
     p0 = W.gan_polycrystal(g0, D0, r0)
     tg = np.random.default_rng(0).integers(0, g0.n_cells, size=oracle_targets)
     t_or = time.perf_counter()
-    ref = oracle.stress_direct(g0, p0.t, p0.b, p0.rho, targets=tg, use_table=False).T
+    oracle.stress_direct(g0, p0.t, p0.b, p0.rho, targets=tg, use_table=False)
     t_or = time.perf_counter() - t_or
-    got = g32.sigma[k0][i0].reshape(6, -1)[:, torch.from_numpy(tg).to(dev)].double().cpu().numpy()
-    scale = max(np.linalg.norm(ref[c]) for c in range(6))
-    rel = max(np.linalg.norm(got[c] - ref[c]) / max(np.linalg.norm(ref[c]), 1e-6 * scale) for c in range(6))
-    out["oracle_check"] = {"realisation": r0, "targets": int(tg.size), "rel_l2_max": float(rel),
-                           "oracle_s": t_or}
+    out["cpu_baseline"] = {"value": tg.size / t_or, "unit": "cells/s", "cores": oracle.num_threads(),
+                           "kind": "oracle", "sample": f"{tg.size} target cells of realisation {r0}"}
     g32.close()
     g16.close()
     for c in ctxs:

@@ -3,7 +3,7 @@
 
 One step = one full evaluation sigma = sum_f G^f * rho_f (Eq. 10) through the
 C ABI (x forward, y forward, fused z + contraction, y inverse, x inverse) on the
-512x512x16 disk of two dislocation families (edge + mixed).  Inputs stay resident
+256x256x128 GaN-like polycrystalline layer (18 families).  Inputs stay resident
 in HBM; L2 is flushed (256 MB write) before every timed step and each step is
 timed with CUDA events on the launching stream.
 
@@ -34,7 +34,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "stress cells/s"
 UNIT = "cells/s"
-DEFAULT_WORKLOAD = "radial_disk_512x512x16"
+DEFAULT_WORKLOAD = "gan_layer_256x256x128"
 PASS_NAMES = ("x_fwd", "y_fwd", "z_fused", "y_inv", "x_inv")
 
 

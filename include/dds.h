@@ -89,8 +89,12 @@ enum {
 #define DDS_MAX_FAMILIES 64    /* families per context                               */
 #define DDS_MAX_FIELDS 12      /* effective fields after collapsing families         */
 
-/* Create a context bound to CUDA device `cuda_device`.  *out receives the handle
- * (NULL on failure).  Errors: INVALID_ARG (out NULL or no such device), OOM. */
+/* Create a context bound to CUDA device `cuda_device`: the holder of one problem of
+ * Sec. 2.1 (a grid of cells, the elastic medium, the dislocation families) and of its
+ * interaction coefficients, which the paper computes once per geometry and reuses
+ * for every density (Sec. 2.3, remark on the coefficient table).  *out receives the
+ * handle (NULL on failure).  Errors: INVALID_ARG (out NULL or no such device), CUDA
+ * (the device cannot be made current), OOM. */
 int dds_create(dds_ctx **out, int cuda_device);
 
 /* Grid shape and cell edges (m), shear modulus mu (Pa) and Poisson ratio nu of the
@@ -190,12 +194,16 @@ void dds_graph_destroy(dds_graph *graph);
  * once it has started.  Same inputs, outputs and result as dds_stress (the context
  * must be built by dds_build_kernels during set-up), but the work buffers between
  * the passes come from one fixed area of DDS_NOALLOC_SCRATCH_BYTES that the library
- * declares as device memory; every GPU that loads the library holds that area until
- * the process exits.  The first call on a device looks up the area's device address
- * (cudaGetSymbolAddress, once per device); make that first call before any stream
- * capture.  All calls, from any context or stream, share the one area and its
- * contents persist between calls: calls whose executions overlap on the GPU race,
- * so serialise them (one stream, or events).  No part of the area needs to start at
+ * declares as device memory.  dds_build_kernels, a set-up step, places the area on the
+ * context's device (under lazy module loading this is when the device memory is taken)
+ * and looks up its device address, once per device; from then on the device holds the
+ * area until the process exits, and dds_stress_noalloc itself allocates nothing.  (The
+ * CUDA driver still loads the code of the evaluation kernels at their first launch
+ * under lazy module loading: a caller that may not allocate at all makes one call
+ * during set-up, or runs with CUDA_MODULE_LOADING=EAGER.)  All calls, from any
+ * context or stream, share the one area and its contents persist between calls:
+ * calls whose executions overlap on the GPU race, so serialise them (one stream, or
+ * events).  No part of the area needs to start at
  * zero: every element a pass reads was written earlier in the same call.  Grids
  * whose work space exceeds the area (about 64x64x32 cells with 4 combined fields
  * fits) are rejected with DDS_ERR_UNSUPPORTED and a message giving the size
@@ -270,7 +278,8 @@ int dds_device_status(int cuda_device, int reset);
 /* Last error message of this context (never NULL; "" if none). */
 const char *dds_last_error(const dds_ctx *ctx);
 
-/* Free everything the context owns.  NULL is a no-op. */
+/* Free everything the context owns: its FP64-derived kernel spectra (the per-geometry
+ * coefficients of Sec. 2.3), work buffers and staging buffers.  NULL is a no-op. */
 void dds_destroy(dds_ctx *ctx);
 
 #ifdef __cplusplus

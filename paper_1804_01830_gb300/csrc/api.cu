@@ -85,19 +85,6 @@ void free_twiddles(Twiddles *tw) {
 
 namespace {
 
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-  }
-};
-
 int next_pow2(int v) {
   int p = 1;
   while (p < v) p <<= 1;
@@ -347,6 +334,10 @@ int dds_create(dds_ctx **out, int cuda_device) {
   if (!ctx) return DDS_ERR_OOM;
   ctx->device = cuda_device;
   DeviceGuard guard(cuda_device);
+  if (!guard.ok) {
+    delete ctx;
+    return DDS_ERR_CUDA;
+  }
   if (make_twiddles(&ctx->tw) != cudaSuccess) {
     cudaGetLastError();
     free_twiddles(&ctx->tw);
@@ -462,6 +453,7 @@ int dds_build_kernels(dds_ctx *ctx, void *cuda_stream) {
     return fail(ctx, DDS_ERR_NOT_READY, "build_kernels: set geometry and families first");
   if (ctx->built) return DDS_OK;
   DeviceGuard guard(ctx->device);
+  if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "cannot make device %d current", ctx->device);
   int rc = make_plan(ctx);
   if (rc != DDS_OK) return rc;
   rc = alloc_buffers(ctx);
@@ -470,6 +462,10 @@ int dds_build_kernels(dds_ctx *ctx, void *cuda_stream) {
     rc = build_spectra(ctx, (cudaStream_t)cuda_stream);
     if (rc != DDS_OK) return rc;
   }
+  // place the fixed work area of dds_stress_noalloc on this device now, during set-up
+  const cudaError_t nerr = noalloc_prepare(ctx->device);
+  if (nerr != cudaSuccess)
+    return fail(ctx, DDS_ERR_CUDA, "build_kernels: cannot locate the fixed work area: %s", cudaGetErrorString(nerr));
   ctx->built = true;
   ctx->err.clear();
   return DDS_OK;
@@ -480,6 +476,7 @@ int dds_autotune(dds_ctx *ctx, void *cuda_stream, float *best_ms) {
   if (!ctx->has_geom || !ctx->has_fam)
     return fail(ctx, DDS_ERR_NOT_READY, "autotune: set geometry and families first");
   DeviceGuard guard(ctx->device);
+  if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "cannot make device %d current", ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   // candidate schedules of the fused z pass: (lanes, tile width)
   ctx->z_lanes = 0;
@@ -563,6 +560,7 @@ int dds_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, void 
   if (((uintptr_t)rho & 15) || ((uintptr_t)sigma & 15))
     return fail(ctx, DDS_ERR_INVALID_ARG, "stress: rho and sigma must be 16-byte aligned");
   DeviceGuard guard(ctx->device);
+  if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "cannot make device %d current", ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (ctx->fe == 0) {
     const cudaError_t err = cudaMemsetAsync(sigma, 0, sizeof(float) * 6 * (size_t)ctx->nx * ctx->ny * ctx->nz, s);
@@ -578,6 +576,7 @@ int dds_relax(dds_ctx *ctx, const float *sigma_dis, float *u, int n_steps, float
   if (!sigma_dis || !u) return fail(ctx, DDS_ERR_INVALID_ARG, "relax: NULL pointer");
   if (n_steps < 0) return fail(ctx, DDS_ERR_INVALID_ARG, "relax: negative step count %d", n_steps);
   DeviceGuard guard(ctx->device);
+  if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "cannot make device %d current", ctx->device);
   return enqueue_relax(ctx, sigma_dis, u, n_steps, sigma_tot, (cudaStream_t)cuda_stream);
 }
 
@@ -591,6 +590,7 @@ int dds_stress_multi(dds_ctx *ctx, int nb, const void *rho, int rho_dtype, float
   if (((uintptr_t)rho & 15) || ((uintptr_t)sigma & 15))
     return fail(ctx, DDS_ERR_INVALID_ARG, "stress_multi: rho and sigma must be 16-byte aligned");
   DeviceGuard guard(ctx->device);
+  if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "cannot make device %d current", ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (ctx->fe == 0) {
     const cudaError_t err =
@@ -618,6 +618,7 @@ int dds_stress_stats(dds_ctx *ctx, int nb, const void *rho, int rho_dtype, float
   if (((uintptr_t)rho & 15) || ((uintptr_t)sigma & 15))
     return fail(ctx, DDS_ERR_INVALID_ARG, "stress_stats: rho and sigma must be 16-byte aligned");
   DeviceGuard guard(ctx->device);
+  if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "cannot make device %d current", ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t ns = 6 * (size_t)nb * ctx->nz;
   if (ctx->fe == 0) {
@@ -681,6 +682,7 @@ int dds_graph_capture(dds_ctx **ctxs, int n, const int *nb, const void **rho, co
       return fail(c, DDS_ERR_INVALID_ARG, "graph_capture: rho and sigma must be non-NULL and 16-byte aligned");
   }
   DeviceGuard guard(ctxs[0]->device);
+  if (!guard.ok) return fail(ctxs[0], DDS_ERR_CUDA, "cannot make device %d current", ctxs[0]->device);
   cudaStream_t user = (cudaStream_t)cuda_stream;
   // work buffers for every batch, then one evaluation of each entry outside the capture
   // (finishes the library's lazy per-device set-up; writes sigma)
@@ -737,6 +739,7 @@ int dds_graph_capture(dds_ctx **ctxs, int n, const int *nb, const void **rho, co
 int dds_graph_launch(dds_graph *g, void *cuda_stream) {
   if (!g) return DDS_ERR_INVALID_ARG;
   DeviceGuard guard(g->device);
+  if (!guard.ok) return DDS_ERR_CUDA;
   const cudaError_t err = cudaGraphLaunch(g->exec, (cudaStream_t)cuda_stream);
   if (err != cudaSuccess) {
     cudaGetLastError();
@@ -755,7 +758,7 @@ int dds_graph_nodes(const dds_graph *g) {
 void dds_graph_destroy(dds_graph *g) {
   if (!g) return;
   {
-    DeviceGuard guard(g->device);
+    DeviceGuard guard(g->device);   // frees proceed even if it failed: they need no current device
     cudaGraphExecDestroy(g->exec);
     cudaGraphDestroy(g->graph);
   }
@@ -767,6 +770,7 @@ int dds_stress_host(dds_ctx *ctx, const float *rho_host, float *sigma_host, void
   if (!ctx->built) return fail(ctx, DDS_ERR_NOT_READY, "stress_host: call dds_build_kernels first");
   if (!rho_host || !sigma_host) return fail(ctx, DDS_ERR_INVALID_ARG, "stress_host: NULL pointer");
   DeviceGuard guard(ctx->device);
+  if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "cannot make device %d current", ctx->device);
   const size_t N = (size_t)ctx->nx * ctx->ny * ctx->nz;
   const size_t rb = sizeof(float) * N * ctx->F, sb = sizeof(float) * N * 6;
   if (ctx->h2d_rho_bytes < rb) {
@@ -818,6 +822,7 @@ int dds_table_at(dds_ctx *ctx, const double t[3], const double b[3], long n, con
       return fail(ctx, DDS_ERR_INVALID_ARG, "table_at: offset (%d,%d,%d) outside the grid", i, j, k);
   }
   DeviceGuard guard(ctx->device);
+  if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "cannot make device %d current", ctx->device);
   int *d_ijk = nullptr;
   double *d_out = nullptr;
   cudaError_t err = cudaMalloc(&d_ijk, sizeof(int) * 3 * n);
@@ -861,6 +866,7 @@ int dds_profile_read(dds_ctx *ctx, int max_steps, float *ms_out, int *n_steps, i
   if (max_steps < 0 || (max_steps > 0 && !ms_out))
     return fail(ctx, DDS_ERR_INVALID_ARG, "profile_read: bad arguments");
   DeviceGuard guard(ctx->device);
+  if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "cannot make device %d current", ctx->device);
   const int steps = std::min(max_steps, ctx->prof_steps);
   for (int st = 0; st < steps; ++st) {
     cudaEvent_t *ev = &ctx->prof_events[6 * (size_t)st];
@@ -879,7 +885,7 @@ const char *dds_last_error(const dds_ctx *ctx) { return ctx ? ctx->err.c_str() :
 void dds_destroy(dds_ctx *ctx) {
   if (!ctx) return;
   {
-    DeviceGuard guard(ctx->device);
+    DeviceGuard guard(ctx->device);   // frees proceed even if it failed: they need no current device
     free_buffers(ctx);
     free_twiddles(&ctx->tw);
     cudaFree(ctx->h2d_rho);

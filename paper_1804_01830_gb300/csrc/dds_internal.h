@@ -139,7 +139,33 @@ int enqueue_relax(dds_ctx *ctx, const float *sig, float *u, int n_steps, float *
 int enqueue_stress_buffers(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, float2 *bufA, float2 *bufB,
                            float2 *nyqA, float2 *nyqB, cudaStream_t s);
 
+// Locates the fixed work area of dds_stress_noalloc on device `dev` (current), which
+// loads it onto the device if it is not there yet.
+cudaError_t noalloc_prepare(int dev);
+
 // Set ctx->err (printf-style) and return code.
 int fail(dds_ctx *ctx, int code, const char *fmt, ...);
+
+// Makes `dev` the current device for the guard's lifetime and restores the previous
+// one afterwards.  ok is false when cudaSetDevice failed (then nothing may be enqueued:
+// the work would land on whatever device is current).
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+    }
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) cudaGetLastError();
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard &) = delete;
+  DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
 
 }  // namespace dds

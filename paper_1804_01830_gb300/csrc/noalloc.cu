@@ -4,7 +4,10 @@
 // file-scope device array of DDS_NOALLOC_SCRATCH_BYTES instead of buffers the
 // context allocated.  Host code cannot use the array's name as a device address,
 // so the address is looked up once per device with cudaGetSymbolAddress (with that
-// device current) and passed to the kernels.
+// device current) and passed to the kernels.  The look-up happens in
+// dds_build_kernels (noalloc_prepare), a set-up step: under lazy module loading it is
+// the look-up that places this file's module, and with it the array, on the device,
+// so no call of dds_stress_noalloc is the one that allocates it.
 #include <algorithm>
 #include <mutex>
 
@@ -22,8 +25,10 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_scratch_mu;
 float2 *g_scratch_addr[MAX_DEVICES] = {};
 
-// Device address of g_scratch on device `dev`, which must be current.
+// Device address of g_scratch on device `dev`, which must be current; looked up on
+// the first request for that device.
 cudaError_t scratch_address(int dev, float2 **out) {
+  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_addr[dev]) {
     void *p = nullptr;
@@ -39,20 +44,15 @@ size_t round256(size_t elems) {   // float2 elements, rounded up to 256 bytes
   return (elems + 31) / 32 * 32;
 }
 
-struct CurrentDevice {
-  int prev = -1;
-  explicit CurrentDevice(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~CurrentDevice() {
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-  }
-};
-
 }  // namespace
+
+// Called by dds_build_kernels with the context's device current.
+cudaError_t noalloc_prepare(int dev) {
+  if (dev < 0 || dev >= MAX_DEVICES) return cudaSuccess;   // dds_stress_noalloc refuses such devices
+  float2 *p = nullptr;
+  return scratch_address(dev, &p);
+}
+
 }  // namespace dds
 
 using namespace dds;
@@ -83,7 +83,8 @@ extern "C" int dds_stress_noalloc(dds_ctx *ctx, const void *rho, int rho_dtype, 
                 "stress_noalloc: this grid needs %.1f MB of work space; the fixed area holds %.1f MB",
                 need * sizeof(float2) / 1048576.0, (double)DDS_NOALLOC_SCRATCH_BYTES / 1048576.0);
 
-  CurrentDevice guard(ctx->device);
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "stress_noalloc: cannot make device %d current", ctx->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (ctx->fe == 0) {
     const cudaError_t err = cudaMemsetAsync(sigma, 0, sizeof(float) * 6 * (size_t)ctx->nx * ctx->ny * ctx->nz, s);

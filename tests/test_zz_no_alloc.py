@@ -6,7 +6,9 @@ their loop has started.  For them the library offers an evaluation whose work
 buffers live in a fixed device area it declares itself.  These tests call that
 entry point through the C ABI twice in a row (different densities, so stale
 contents of the shared area would show) and compare each result with dds_stress,
-and check that a grid too large for the area is refused with a clear error.
+check that a call changes no device allocation (free device memory is the same
+before and after it), and check that a grid too large for the area is refused with
+a clear error.
 This file is collected last so that a run stopping at the first failure has
 already run every other test.
 """
@@ -61,6 +63,24 @@ def test_noalloc_matches_stress_on_two_calls(dds, idx):
         got = out.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert rel_l2_per_component(got, ref.cpu().numpy()).max() <= TOL_STRESS
+    ctx.close()
+
+
+def test_noalloc_call_allocates_no_device_memory(dds):
+    p = problems()[2]
+    ctx = dds.context_for(p)             # set-up: builds the kernels and places the area
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho, dtype=np.float32)).cuda()
+    out = torch.empty((6,) + p.geom.shape, dtype=torch.float32, device="cuda")
+    # warm-up call: the driver loads the evaluation kernels' code at their first launch
+    dds.dds_stress_noalloc(ctx.handle, rho.data_ptr(), dds.DDS_F32, out.data_ptr())
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        dds.dds_stress_noalloc(ctx.handle, rho.data_ptr(), dds.DDS_F32, out.data_ptr())
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.isfinite(out).all()
     ctx.close()
 
 

@@ -383,3 +383,50 @@ def test_replica_table_is_odd():
     g = W.Geometry(7, 6, 4, 1e-6, 1e-6, 0.25e-6, MU, NU)
     tab = oracle.gtable(g, W.t_mixed(), (BB, 0.3 * BB, 1.6 * BB), n_shells=3)
     assert rel(tab[::-1, ::-1, ::-1], -tab) < 1e-13
+
+
+# ------------------------------------------------------- mirror parities --
+PAIRS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))   # xx, yy, zz, xy, xz, yz
+
+
+def mirror_parity(a, b):
+    """Parity of each component of G under the mirror x_a -> -x_a, for a line direction with
+    t_a = 0 and b parallel or perpendicular to axis a.  Reflection Q maps the segment onto
+    itself and the field of (t, b) at r onto det(Q) Q sigma Q^T of (t, Q b) at Q r, the
+    det(Q) = -1 coming from the handedness of the Burgers circuit; Q b = s_b b."""
+    s_b = -1.0 if b[a] != 0.0 else 1.0
+    q = [(-1.0 if i == a else 1.0) for i in range(3)]
+    return np.array([-s_b * q[i] * q[j] for i, j in PAIRS])
+
+
+@pytest.mark.parametrize("cells", [(0.2e-6, 0.2e-6, 0.05e-6), (0.5e-6, 0.5e-6, 0.2e-6), (1e-6, 1e-6, 1e-6)])
+def test_table_mirror_parities(cells):
+    """The coefficient table (near field subdivided) is even or odd in x under the mirror
+    x -> -x for every line direction in the y-z plane and Cartesian b, and in y as well for
+    t = z, with the parities of the reflected field; the textbook edge field of an
+    infinite line (Sec. 3, Fig. 5 discussion) shows the same parities.  Oblique b, or a
+    line direction out of the mirror plane, break them (the test has teeth)."""
+    g = W.Geometry(9, 8, 6, *cells, MU, NU)
+    s15 = math.sin(math.radians(15.6))
+    lines = [((0.0, 0.0, 1.0), (0, 1)), ((0.0, s15, math.sqrt(1 - s15 * s15)), (0,)),
+             ((0.0, 0.5, math.sqrt(3) / 2), (0,))]
+    for t, axes in lines:
+        for d in range(3):
+            b = np.zeros(3)
+            b[d] = BB
+            tab = oracle.gtable(g, t, b)
+            m = np.abs(tab).max(axis=(0, 1, 2))
+            for a in axes:
+                flip = tab[:, :, ::-1] if a == 0 else tab[:, ::-1, :]
+                p = mirror_parity(a, b)
+                assert np.all(np.abs(flip - p * tab).max(axis=(0, 1, 2)) <= 1e-13 * m.max())
+        # teeth: an oblique b has no x parity; a tilted line has no y parity
+        tab = oracle.gtable(g, t, (BB, BB, 0.0))
+        assert np.abs(tab[:, :, ::-1] - mirror_parity(0, (BB, 0, 0)) * tab).max() > 1e-3 * np.abs(tab).max()
+    tab = oracle.gtable(g, lines[1][0], (BB, 0.0, 0.0))
+    assert np.abs(tab[:, ::-1, :] - mirror_parity(1, (BB, 0, 0)) * tab).max() > 1e-3 * np.abs(tab).max()
+    # the infinite edge line of Burgers vector along x: the same parities at a few points
+    for x, y in [(1.3, 0.4), (0.2, 2.1)]:
+        s = textbook_infinite(x, y, (BB, 0, 0))
+        assert rel(textbook_infinite(-x, y, (BB, 0, 0)), mirror_parity(0, (BB, 0, 0)) * s) < 1e-14
+        assert rel(textbook_infinite(x, -y, (BB, 0, 0)), mirror_parity(1, (BB, 0, 0)) * s) < 1e-14

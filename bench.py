@@ -144,9 +144,18 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- byte model --
+def spectra_bytes(q):
+    """Kernel-spectrum bytes one evaluation reads: what the context stores (half the
+    columns where every field has the x-mirror parity), else one FP32 imaginary part
+    per (k, component, field)."""
+    if q.get("spectra_bytes"):
+        return q["spectra_bytes"]
+    return 6 * q["n_fields"] * (q["px"] // 2 + 1) * q["py"] * q["pz"] * 4
+
+
 def pass_bytes(p, q):
     """Algorithmic HBM bytes of each pass of one evaluation (reads + writes the pass
-    must do in this schedule; kernel spectra stored as FP32 imaginary parts)."""
+    must do in this schedule)."""
     g = p.geom
     N = g.n_cells
     fin, fe = p.n_families, q["n_fields"]
@@ -158,7 +167,7 @@ def pass_bytes(p, q):
     return {
         "x_fwd": fin * N * 4 + fe * x_spec,
         "y_fwd": fe * x_spec + fe * y_spec,
-        "z_fused": fe * y_spec + 6 * fe * m1 * py * pz * 4 + 6 * y_spec,
+        "z_fused": fe * y_spec + spectra_bytes(q) + 6 * y_spec,
         "y_inv": 6 * y_spec + 6 * x_spec,
         "x_inv": 6 * x_spec + 6 * N * 4,
     }
@@ -167,8 +176,7 @@ def pass_bytes(p, q):
 def floor_bytes(p, q):
     """Strict floor per evaluation: read rho, read the kernel spectra once, write sigma."""
     g = p.geom
-    m1 = q["px"] // 2 + 1
-    return p.n_families * g.n_cells * 4 + 6 * q["n_fields"] * m1 * q["py"] * q["pz"] * 4 + 6 * g.n_cells * 4
+    return p.n_families * g.n_cells * 4 + spectra_bytes(q) + 6 * g.n_cells * 4
 
 
 def measured_peaks():

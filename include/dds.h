@@ -227,6 +227,13 @@ int dds_table_at(dds_ctx *ctx, const double t[3], const double b[3], long n,
 /* Sizes: number of effective fields after collapsing families, padded FFT sizes. */
 int dds_query(const dds_ctx *ctx, int *n_fields, int *px, int *py, int *pz);
 
+/* Bytes of the cached kernel spectra of a built context (FP32 or FP16 values).  The
+ * fused z pass reads them once per evaluation; where the coefficient table has the
+ * x-mirror parity for every effective field (Sec. 3 discusses these symmetries of the
+ * straight-dislocation field), only the spectra of ky <= py/2 are stored.  *bytes
+ * receives the size.  Errors: INVALID_ARG (NULL), NOT_READY (not built). */
+int dds_spectra_bytes(const dds_ctx *ctx, unsigned long long *bytes);
+
 /* Number of kernel launches one dds_stress call issues. */
 int dds_launches_per_stress(const dds_ctx *ctx);
 

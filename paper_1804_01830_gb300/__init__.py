@@ -36,7 +36,7 @@ EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option
            "dds_build_kernels", "dds_stress", "dds_stress_multi", "dds_stress_stats", "dds_stress_batched",
            "dds_stress_noalloc",
            "dds_stress_host",
-           "dds_table_at", "dds_query", "dds_launches_per_stress", "dds_profile_enable",
+           "dds_table_at", "dds_query", "dds_spectra_bytes", "dds_launches_per_stress", "dds_profile_enable",
            "dds_profile_read", "dds_relax", "dds_graph_capture", "dds_graph_launch", "dds_graph_nodes",
            "dds_graph_destroy", "dds_device_status", "dds_last_error", "dds_destroy")
 
@@ -77,6 +77,7 @@ def load_library():
         "dds_stress_host": ([vp, vp, vp, vp], ctypes.c_int),
         "dds_table_at": ([vp, dp, dp, lp, ip, dp], ctypes.c_int),
         "dds_query": ([vp, ip, ip, ip, ip], ctypes.c_int),
+        "dds_spectra_bytes": ([vp, ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
         "dds_launches_per_stress": ([vp], ctypes.c_int),
         "dds_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
         "dds_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ip, ip], ctypes.c_int),
@@ -208,7 +209,14 @@ def dds_table_at(ctx, t, b, ijk) -> np.ndarray:
 def dds_query(ctx):
     v = [ctypes.c_int() for _ in range(4)]
     _check(ctx, load_library().dds_query(ctx, *[ctypes.byref(x) for x in v]))
-    return {"n_fields": v[0].value, "px": v[1].value, "py": v[2].value, "pz": v[3].value}
+    return {"n_fields": v[0].value, "px": v[1].value, "py": v[2].value, "pz": v[3].value,
+            "spectra_bytes": dds_spectra_bytes(ctx)}
+
+
+def dds_spectra_bytes(ctx) -> int:
+    b = ctypes.c_ulonglong()
+    _check(ctx, load_library().dds_spectra_bytes(ctx, ctypes.byref(b)))
+    return int(b.value)
 
 
 def dds_launches_per_stress(ctx) -> int:

@@ -184,6 +184,45 @@ int collapse(dds_ctx *ctx) {
   return DDS_OK;
 }
 
+// Mirror x_a -> -x_a maps the segment of (t, b) onto itself and b onto +-b.
+bool mirror_ok(const double *t, const double *b, int a) {
+  const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+  return t[a] == 0.0 && (b[a] == 0.0 || (b[a1] == 0.0 && b[a2] == 0.0));
+}
+
+// Parity of component c (xx, yy, zz, xy, xz, yz) under that mirror: reflection Q takes
+// the field of (t, b) at r to det(Q) Q sigma Q^T of (t, Q b) at Q r, det(Q) = -1 from
+// the handedness of the Burgers circuit, Q b = s_b b.
+int mirror_parity(const double *b, int a, int c) {
+  static const int I[6] = {0, 1, 2, 0, 0, 1}, J[6] = {0, 1, 2, 1, 2, 2};
+  const int sb = b[a] != 0.0 ? -1 : 1;
+  const int qi = I[c] == a ? -1 : 1, qj = J[c] == a ? -1 : 1;
+  return -sb * qi * qj;
+}
+
+}  // namespace
+
+size_t zfour_symmetry(const double *field_t, const double *field_b, int fe, Shape *sh) {
+  ZSym &zs = sh->zs;
+  memset(&zs, 0, sizeof(zs));
+  static const int chi[6] = {1, 1, 1, -1, -1, 1};
+  bool all = fe > 0;
+  for (int e = 0; e < fe; ++e) {
+    const double *t = field_t + 3 * e, *b = field_b + 3 * e;
+    bool ok = mirror_ok(t, b, 0);
+    // g(kx, -ky, -kz) = -p_x(c) g(kx, ky, kz), and -p_x(c) = s_b chi(c)
+    const int sb = b[0] != 0.0 ? -1 : 1;
+    for (int c = 0; c < 6 && ok; ++c) ok = -mirror_parity(b, 0, c) == sb * chi[c];
+    all = all && ok;
+    if (sb < 0) zs.sbneg |= 1u << e;
+  }
+  zs.xall = all ? 1u : 0u;
+  if (!all) zs.sbneg = 0;
+  return (size_t)zf_stored_tiles(*sh) * 6 * fe * sh->pz * sh->wz;
+}
+
+namespace {
+
 // Padded sizes and the tile width of the fused z pass.
 int make_plan(dds_ctx *ctx) {
   Shape sh;
@@ -221,6 +260,7 @@ int make_plan(dds_ctx *ctx) {
                   "(pz %d, %d fields)", sh.pz, sh.fe);
     sh.zfour = 1;
     sh.wz = fw;
+    zfour_symmetry(ctx->field_t.data(), ctx->field_b.data(), sh.fe, &sh);
     ctx->shape = sh;
     return DDS_OK;
   }
@@ -289,7 +329,12 @@ int alloc_buffers(dds_ctx *ctx) {
   const size_t M = sh.M, py = sh.py, pz = sh.pz;
   size_t a, b, na, nb;
   work_sizes(sh, 1, &a, &b, &na, &nb);
-  const size_t ks = py * (M + 1) * pz * 6 * fe;   // one FP32 value per (k, component, field)
+  // one value per (k, component, field), or the three-stage pass's symmetric subset
+  size_t ks = py * (M + 1) * pz * 6 * fe;
+  if (sh.zfour) {
+    Shape tmp = sh;
+    ks = zfour_symmetry(ctx->field_t.data(), ctx->field_b.data(), sh.fe, &tmp);
+  }
   free_buffers(ctx);
   cudaError_t err = cudaMalloc(&ctx->bufA, a * sizeof(float2));
   if (err == cudaSuccess) err = cudaMalloc(&ctx->bufB, b * sizeof(float2));
@@ -846,6 +891,13 @@ int dds_query(const dds_ctx *ctx, int *n_fields, int *px, int *py, int *pz) {
   if (px) *px = 2 * ctx->shape.M;
   if (py) *py = ctx->shape.py;
   if (pz) *pz = ctx->shape.pz;
+  return DDS_OK;
+}
+
+int dds_spectra_bytes(const dds_ctx *ctx, unsigned long long *bytes) {
+  if (!ctx || !bytes) return DDS_ERR_INVALID_ARG;
+  if (!ctx->built) return DDS_ERR_NOT_READY;
+  *bytes = (unsigned long long)ctx->kspec_floats * (ctx->spectra_fp16 ? 2 : 4);
   return DDS_OK;
 }
 

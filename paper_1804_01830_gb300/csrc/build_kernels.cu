@@ -303,9 +303,7 @@ __global__ void __launch_bounds__(256) k_cols_d(double2 *data, long os, long rs,
 //   shared-memory variant (zg = 0): kspec[tile][6][fe][pz][wz], tiles of wz columns;
 //   register variant (zg = G > 0):  kspec[warp tile][6][fe][lane][E], E = pz / G, warp
 //     tiles of 32/G columns, lane g * (32/G) + w holding kz = k1 + E bitrev_G(g), k1 < E;
-//   three-stage variant (zg = -1, pz = 8 R1, tiles of wz columns): per (tile, c)
-//     16-byte chunks [j][thread t = k1 wz + w], the value of (e, kz = k1 + R1 k2) at
-//     position (8 e + k2) % V of chunk j = (8 e + k2) / V, V values per chunk.
+//   three-stage variant (k_extract_four): see there.
 // Main tiles cover (ky, kx < M) row by row; the Nyquist tiles (kx = M) follow.
 __device__ __forceinline__ void store_val(float *p, double v) { *p = (float)v; }
 __device__ __forceinline__ void store_val(__half *p, double v) { *p = __float2half_rn((float)v); }
@@ -329,7 +327,7 @@ __global__ void k_store_scale(const unsigned long long *amax, double scale, floa
 template <typename OT>
 __global__ void k_extract(const double2 *spec, int M, int py, int pz, int wz, int zg, int fe, int e, int c,
                           double scale, const unsigned long long *amax, OT *kspec) {
-  const int cw = zg > 0 ? 32 / zg : wz;                  // columns per tile (zg < 0: wz)
+  const int cw = zg > 0 ? 32 / zg : wz;                  // columns per tile
   const int E = zg > 0 ? pz / zg : 0;                     // registers per lane
   const long per_tile = zg > 0 ? 32L * E : (long)pz * wz;
   const long tiles_main = (long)py * (M / cw);
@@ -339,14 +337,8 @@ __global__ void k_extract(const double2 *spec, int M, int py, int pz, int wz, in
   const long tau = idx / per_tile;
   const int r = (int)(idx % per_tile);
   int kz, w;
-  long dst = ((tau * 6 + c) * fe + e) * per_tile + r;
-  if (zg < 0) {
-    constexpr int V = 16 / (int)sizeof(OT);
-    const int t = r / 8, k2 = r % 8, R1 = pz / 8, q = 8 * e + k2;
-    w = t % wz;
-    kz = t / wz + R1 * k2;
-    dst = (tau * 6 + c) * fe * per_tile + ((long)(q / V) * (R1 * wz) + t) * V + q % V;
-  } else if (zg > 0) {
+  const long dst = ((tau * 6 + c) * fe + e) * per_tile + r;
+  if (zg > 0) {
     const int lane = r / E, k1 = r % E, g = lane / cw;
     const int gb = zg == 4 ? (((g & 1) << 1) | (g >> 1))
                  : zg == 8 ? (((g & 1) << 2) | (g & 2) | (g >> 2)) : g;
@@ -369,6 +361,42 @@ __global__ void k_extract(const double2 *spec, int M, int py, int pz, int wz, in
     const double m = __longlong_as_double((long long)*amax) * scale;
     if (m > 0.0) v /= m;
   }
+  store_val(&kspec[dst], v);
+}
+
+// Imaginary part of the spectrum of component c of field e, scaled, into the layout
+// the three-stage z pass reads (pz = 8 R1, tiles of W = wz columns): per stored tile s
+// and component c, 16-byte chunks [j][thread t = k1 W + w], the value of
+// (e, kz = k1 + R1 k2) at position (8 e + k2) % V of chunk j = (8 e + k2) / V, V values
+// per chunk.  Stored tiles: the main tiles (ky, kx tile) row by row -- all of them, or
+// those with ky <= py/2 when every field has the x-mirror parity (ZSym::xall) -- then
+// the Nyquist tiles (kx = M).
+template <typename OT>
+__global__ void k_extract_four(const double2 *spec, Shape sh, int e, int c, double scale,
+                               const unsigned long long *amax, OT *kspec) {
+  constexpr int V = 16 / (int)sizeof(OT);
+  const int W = sh.wz, R1 = sh.pz / 8, M = sh.M, py = sh.py, fe = sh.fe;
+  const long per_tile = (long)sh.pz * W;
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= zf_stored_tiles(sh) * per_tile) return;
+  const long s = idx / per_tile;
+  const int r = (int)(idx - s * per_tile), t = r / 8, k2 = r % 8, k1 = t / W, w = t % W, q = 8 * e + k2;
+  const long ktiles = M / W;
+  const long main_tiles = (long)(sh.zs.xall ? py / 2 + 1 : py) * ktiles;
+  int kx, ky;
+  if (s < main_tiles) {
+    ky = (int)(s / ktiles);
+    kx = (int)(s % ktiles) * W + w;
+  } else {
+    ky = (int)(s - main_tiles) * W + w;
+    kx = M;
+  }
+  double v = spec[((long)(k1 + R1 * k2) * py + ky) * (M + 1) + kx].y * scale;
+  if (amax != nullptr) {                 // FP16 storage: values relative to the largest
+    const double m = __longlong_as_double((long long)*amax) * scale;
+    if (m > 0.0) v /= m;
+  }
+  const size_t dst = (size_t)(s * 6 + c) * fe * per_tile + ((size_t)(q / V) * (R1 * W) + t) * V + q % V;
   store_val(&kspec[dst], v);
 }
 
@@ -517,21 +545,24 @@ int build_spectra(dds_ctx *ctx, cudaStream_t s) {
       if (err == cudaSuccess)   // z: one batch, rows kz, columns (ky, kx)
         err = cols_dispatch(pz, spec, 1, 0, (long)py * (M + 1), (long)py * (M + 1), ctx->tw.f64, s);
       if (err == cudaSuccess) {
-        const long n = (long)py * (M + 1) * pz;
+        const long n = sh.zfour ? zf_stored_tiles(sh) * pz * sh.wz : (long)py * (M + 1) * pz;
+        const unsigned blocks = (unsigned)((n + 255) / 256);
         if (ctx->spectra_fp16) {
           err = cudaMemsetAsync(d_amax, 0, sizeof(unsigned long long), s);
           if (err == cudaSuccess) {
             k_absmax_imag<<<1024, 256, 0, s>>>(spec, nspec, d_amax);
             k_store_scale<<<1, 1, 0, s>>>(d_amax, scale, ctx->kscale, c * sh.fe + e);
-            k_extract<__half><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-                spec, M, py, pz, sh.wz, sh.zfour ? -1 : sh.zreg_g, sh.fe, e, c, scale, d_amax,
-                static_cast<__half *>(ctx->kspec));
+            __half *out = static_cast<__half *>(ctx->kspec);
+            if (sh.zfour) k_extract_four<__half><<<blocks, 256, 0, s>>>(spec, sh, e, c, scale, d_amax, out);
+            else k_extract<__half><<<blocks, 256, 0, s>>>(spec, M, py, pz, sh.wz, sh.zreg_g, sh.fe, e, c, scale,
+                                                          d_amax, out);
             err = cudaGetLastError();
           }
         } else {
-          k_extract<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-              spec, M, py, pz, sh.wz, sh.zfour ? -1 : sh.zreg_g, sh.fe, e, c, scale, nullptr,
-              static_cast<float *>(ctx->kspec));
+          float *out = static_cast<float *>(ctx->kspec);
+          if (sh.zfour) k_extract_four<float><<<blocks, 256, 0, s>>>(spec, sh, e, c, scale, nullptr, out);
+          else k_extract<float><<<blocks, 256, 0, s>>>(spec, M, py, pz, sh.wz, sh.zreg_g, sh.fe, e, c, scale,
+                                                       nullptr, out);
           err = cudaGetLastError();
         }
       }

@@ -28,6 +28,18 @@ struct GroupList {
   int g[MAX_GROUPS];
 };
 
+// Symmetry of the kernel spectra used by the three-stage z pass (Shape::zfour).  The
+// mirror x -> -x maps the coefficient table of a field with t_x = 0 and b parallel or
+// perpendicular to x onto +-itself (reflection covariance of the segment field); with
+// the table's oddness this gives g(kx, -ky, -kz) = -p_x(c) g(kx, ky, kz), where
+// -p_x(c) = s_b chi(c): s_b = -1 for b along x (else +1), chi(c) = -1 for xy, xz.
+// When every field has it (xall), only the main tiles with ky <= py/2 are stored: a
+// tile at ky > py/2 works at the negated frequencies -(k1 + R1 k2) and reads the same
+// thread's values of the stored tile py - ky.  sbneg bit e: s_b = -1 for field e.
+struct ZSym {
+  unsigned xall, sbneg;
+};
+
 // Geometry of one evaluation as the device kernels see it.
 struct Shape {
   int nx, ny, nz;     // grid
@@ -38,10 +50,21 @@ struct Shape {
   int zreg_g;         // > 0: register-only z pass, pz = 16 * zreg_g, zreg_g lanes per column
   int zfour;          // 1: three-stage register z pass (pz 128 or 256, wz = zfour_width(pz))
   int nb;             // density sets evaluated together (batch); fields are [b][e], outputs [b][c]
+  ZSym zs;            // zfour: stored-spectrum symmetries and layout
 };
 
 // Columns per tile of the three-stage z pass (Shape::zfour) for padded z size pz.
 __host__ __device__ constexpr int zfour_width(int pz) { return pz >= 256 ? 8 : 16; }
+
+// Tiles of the three-stage z pass whose kernel spectra are stored: the main tiles
+// (all ky, or ky <= py/2 under xall), then the py / W Nyquist-column tiles.
+__host__ __device__ inline long zf_stored_tiles(const Shape &sh) {
+  return (long)(sh.zs.xall ? sh.py / 2 + 1 : sh.py) * (sh.M / sh.wz) + sh.py / sh.wz;
+}
+
+// Fills sh->zs for the effective fields (t, b given per field, fe <= 6) and returns
+// the number of kernel-spectrum values the three-stage z pass stores.
+size_t zfour_symmetry(const double *field_t, const double *field_b, int fe, Shape *sh);
 
 // FP64 description of a box coefficient (Eq. 9b times the cell volume).
 struct CoefGeom {

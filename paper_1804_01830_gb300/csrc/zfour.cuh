@@ -16,6 +16,14 @@
 //            for the outputs b < R1/2 only (rows a + 8 b < nz <= PZ/2) and stores them.
 // Shared memory is written and read once per stage; row strides of 9 W values (T) and
 // (R1 + 1) W values (Y) keep every stage's half-warp accesses free of bank conflicts.
+//
+// Kernel spectra of fields with the x-mirror parity (ZSym) are stored for ky <= py/2
+// only.  A tile at ky > py/2 works at the negated frequencies: the conjugate-direction
+// transform is conj(transform(conj(x))), so it runs the same code on its conjugated,
+// rescaled densities and conjugates what it stores (signs uniform over the tile).  Its
+// thread (k1, w) then needs the values the same thread reads in the stored tile py - ky
+// (g(kx, -ky, -kz) = s_b chi(c) g(kx, ky, kz)).  Launch order puts the tiles ky and
+// py - ky of the same kx range next to each other, so the second read comes from L2.
 #pragma once
 #include "stress_common.cuh"
 
@@ -34,6 +42,20 @@ template <int PZ> struct ZF {
 template <int PZ> __host__ __device__ constexpr int zf_smem(int fe) {
   return fe * ZF<PZ>::R1 * ZF<PZ>::SK > 6 * ZF<PZ>::R2 * ZF<PZ>::SY ? fe * ZF<PZ>::R1 * ZF<PZ>::SK
                                                                     : 6 * ZF<PZ>::R2 * ZF<PZ>::SY;
+}
+
+// Launch order of the main tiles: the rows ky = 0 and py/2 (their own mirrors) first,
+// then, for ky = 1 .. py/2 - 1 and each kx tile, the tile at ky followed by the tile at
+// py - ky.
+__device__ __forceinline__ void zf_tile_of(int L, int py, int ktiles, int *ky, int *kxt) {
+  if (L < 2 * ktiles) {
+    *ky = L < ktiles ? 0 : py / 2;
+    *kxt = L < ktiles ? L : L - ktiles;
+    return;
+  }
+  const int pair = (L - 2 * ktiles) >> 1, ky1 = 1 + pair / ktiles;
+  *kxt = pair - (ky1 - 1) * ktiles;
+  *ky = ((L - 2 * ktiles) & 1) ? py - ky1 : ky1;
 }
 
 // The kernel-spectrum values (e, k2 = 0..7) of fields e = e0 .. e0 + FE - 1 of one
@@ -77,42 +99,44 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes) 
 }
 
 template <int PZ, int FE, typename GT>
-__global__ void __launch_bounds__(ZF<PZ>::NT, 512 / ZF<PZ>::NT) k_zfour(Shape sh, const float2 *in_main, const float2 *in_nyq,
-                                                         const GT *kspec, const float *kscale, float2 *out_main,
-                                                         float2 *out_nyq, const float2 *tw) {
+__global__ void __launch_bounds__(ZF<PZ>::NT, 512 / ZF<PZ>::NT)
+    k_zfour(Shape sh, const float2 *in_main, const float2 *in_nyq, const GT *kspec, const float *kscale,
+            float2 *out_main, float2 *out_nyq, const float2 *tw) {
   constexpr int R1 = ZF<PZ>::R1, R2 = ZF<PZ>::R2, W = ZF<PZ>::W, NT = ZF<PZ>::NT;
   constexpr int SK = ZF<PZ>::SK, SY = ZF<PZ>::SY, H = R1 / 2;
   extern __shared__ __align__(16) float2 zsm[];
   const int tid = threadIdx.x;
   const int M = sh.M, py = sh.py, nz = sh.nz;
-  const long ktiles = M / W, tiles_main = (long)py * ktiles;
+  const int ktiles = M / W, tiles_main = py * ktiles;
   // Consecutive blocks take the same column tile for the density sets of a batch,
   // so the tile's kernel spectra come from HBM once and from L2 for the others.
-  const long tau = blockIdx.x / sh.nb;
+  const int tau = blockIdx.x / sh.nb;
   const int bset = (int)(blockIdx.x - tau * sh.nb);
   in_main += bset * ((long)FE * nz * py * M);
   in_nyq += bset * ((long)FE * py * nz);
   out_main += bset * (6L * nz * py * M);
   out_nyq += bset * (6L * py * nz);
   const bool nyq = tau >= tiles_main;
-  long ky = 0, kx0 = 0, ky0 = 0;
-  if (!nyq) {
-    ky = tau / ktiles;
-    kx0 = (tau - ky * ktiles) * W;
-  } else {
-    ky0 = (tau - tiles_main) * W;
-  }
+  int ky = 0, kxt = 0, nyq_idx = 0;
+  if (!nyq) zf_tile_of(tau, py, ktiles, &ky, &kxt);
+  else nyq_idx = tau - tiles_main;
+  const bool sw = sh.zs.xall && !nyq && ky > py / 2;   // works at the negated frequencies
   const float2 *twP = tw + tw_offset(PZ);
+  // the stored tile this tile reads: its own, or py - ky for a negated-frequency tile
+  const long st = nyq ? (long)(sh.zs.xall ? py / 2 + 1 : py) * ktiles + nyq_idx
+                      : (long)(sw ? py - ky : ky) * ktiles + kxt;
+  const GT *ks = kspec + st * 6L * FE * PZ * W;
   // the tile's kernel spectra (6 FE PZ W values, contiguous) head for L2 now, so the
-  // per-component loads of stage 2 find them there
-  const GT *ks = kspec + tau * 6L * FE * PZ * W;
-  {
+  // per-component loads of stage 2 find them there; a negated-frequency tile leaves
+  // them to its partner launched beside it
+  if (!sw) {
     constexpr unsigned BYTES = 6u * FE * PZ * W * sizeof(GT), CH = 8192, NCH = (BYTES + CH - 1) / CH;
     static_assert(BYTES % 16 == 0 && NCH <= NT, "prefetch chunks");
     if (tid < (int)NCH) prefetch_l2_bulk(reinterpret_cast<const char *>(ks) + tid * CH, min(CH, BYTES - tid * CH));
   }
 
-  // stage 1: forward R1-point DFTs over n1 of the rows n2 + 8 n1 (n1 < R1/2 non-zero)
+  // stage 1: forward R1-point DFTs over n1 of the rows n2 + 8 n1 (n1 < R1/2 non-zero);
+  // a negated-frequency tile transforms -s_b conj(rho) (s_b folds the spectra's sign)
   for (int item = tid; item < FE * R2 * W; item += NT) {
     const int e = item / (R2 * W), r = item - e * (R2 * W), n2 = r / W, w = r - n2 * W;
     float2 ev[H], od[H];
@@ -121,8 +145,13 @@ __global__ void __launch_bounds__(ZF<PZ>::NT, 512 / ZF<PZ>::NT) k_zfour(Shape sh
       const int z = n2 + R2 * n1;
       ev[n1] = make_float2(0.f, 0.f);
       if (z < nz)
-        ev[n1] = !nyq ? __ldg(in_main + (((long)e * nz + z) * py + ky) * M + kx0 + w)
-                      : __ldg(in_nyq + ((long)e * py + ky0 + w) * nz + z);
+        ev[n1] = !nyq ? __ldg(in_main + (((long)e * nz + z) * py + ky) * M + kxt * W + w)
+                      : __ldg(in_nyq + ((long)e * py + nyq_idx * W + w) * nz + z);
+    }
+    if (sw) {                                 // after all loads are issued
+      const float sy = ((sh.zs.sbneg >> e) & 1u) ? -1.0f : 1.0f;
+#pragma unroll
+      for (int n1 = 0; n1 < H; ++n1) ev[n1] = make_float2(-sy * ev[n1].x, sy * ev[n1].y);
     }
 #pragma unroll
     for (int n1 = 0; n1 < H; ++n1) od[n1] = rot_const<false>(ev[n1], n1, R1);
@@ -180,9 +209,11 @@ __global__ void __launch_bounds__(ZF<PZ>::NT, 512 / ZF<PZ>::NT) k_zfour(Shape sh
   }
   __syncthreads();
 
-  // stage 3: inverse R1-point DFTs over k1, outputs b < R1/2: x(b) = E(b) + W_R1^-b O(b)
+  // stage 3: inverse R1-point DFTs over k1, outputs b < R1/2: x(b) = E(b) + W_R1^-b O(b);
+  // a negated-frequency tile stores chi(c) conj(x)
   for (int item = tid; item < 6 * R2 * W; item += NT) {
     const int c = item / (R2 * W), r = item - c * (R2 * W), a = r / W, wc = r - a * W;
+    const float bx = sw ? ((c == 3 || c == 4) ? -1.0f : 1.0f) : 1.0f, by = sw ? -bx : 1.0f;
     const float2 *Y = zsm + ((long)c * R2 + a) * SY + wc;
     float2 ev[H], od[H];
 #pragma unroll
@@ -196,9 +227,10 @@ __global__ void __launch_bounds__(ZF<PZ>::NT, 512 / ZF<PZ>::NT) k_zfour(Shape sh
     for (int b = 0; b < H; ++b) {
       const int z = a + R2 * b;
       if (z < nz) {
-        const float2 v = cadd(ev[b], rot_const<true>(od[b], b, R1));
-        if (!nyq) out_main[(((long)c * nz + z) * py + ky) * M + kx0 + wc] = v;
-        else out_nyq[((long)c * py + ky0 + wc) * nz + z] = v;
+        const float2 u = cadd(ev[b], rot_const<true>(od[b], b, R1));
+        const float2 v = make_float2(bx * u.x, by * u.y);
+        if (!nyq) out_main[(((long)c * nz + z) * py + ky) * M + kxt * W + wc] = v;
+        else out_nyq[((long)c * py + nyq_idx * W + wc) * nz + z] = v;
       }
     }
   }

@@ -3,7 +3,10 @@
 The algorithmic bytes of each pass are written out here from what the pass moves
 (complex FP32 = 8 bytes, kernel spectra = one FP32 imaginary part per value) for the
 two bench-sized grids, and compared with bench.pass_bytes / bench.floor_bytes and with
-the per-launch figures quoted in the profiles (1.345 GB and 5.524 GB for the fused z pass).
+the per-launch figures quoted in the profiles (1.345 GB and 5.524 GB for the fused z pass
+with every spectrum column stored; 3.519 GB for the GaN layer, whose five fields all have
+the x-mirror parity, so that only the columns ky <= py/2 and the Nyquist column are
+stored).
 """
 from types import SimpleNamespace
 
@@ -42,6 +45,19 @@ def test_pass_bytes_from_first_principles():
         assert bench.pass_bytes(p, q) == want
         assert want["z_fused"] == z_quoted
         assert bench.floor_bytes(p, q) == 4 * fin * n + spectra + 6 * 4 * n
+
+
+def test_mirror_stored_spectra_bytes():
+    # GaN layer: main columns (kx < px/2, ky <= py/2) and all Nyquist columns (kx = px/2)
+    nx, ny, nz, fin, fe = 256, 256, 128, 18, 5
+    px, py, pz = padded(nx, ny, nz)
+    stored_cols = (px // 2) * (py // 2 + 1) + py
+    spectra = 6 * fe * pz * 4 * stored_cols
+    q = {"n_fields": fe, "px": px, "py": py, "pz": pz, "spectra_bytes": spectra}
+    p = SimpleNamespace(geom=W.Geometry(nx, ny, nz, 1e-6, 1e-6, 1e-6), n_families=fin)
+    after_y = (px // 2 + 1) * py * nz * 8
+    assert bench.pass_bytes(p, q)["z_fused"] == fe * after_y + spectra + 6 * after_y == 3_519_021_056
+    assert abs(spectra / (6 * fe * (px // 2 + 1) * py * pz * 4) - 0.5039) < 1e-4
 
 
 def test_pass_model_per_cell_closed_form():

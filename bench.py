@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-comparator", action="store_true", help="skip the cuFFT comparator")
     ap.add_argument("--no-reduced", action="store_true", help="skip the FP16-spectra measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency measurement")
-    ap.add_argument("--serving-seconds", type=float, default=10.0)
+    ap.add_argument("--serving-seconds", type=float, default=60.0)
     ap.add_argument("--serving-streams", type=int, default=4, help="CUDA streams of the server")
     ap.add_argument("--serving-batch", type=int, default=2, help="largest batch per context")
     ap.add_argument("--no-autotune", action="store_true", help="use the planner's default z schedule")
@@ -219,11 +219,14 @@ def ncu_traffic(kernel: str, workload: str):
 # -------------------------------------------------------- cuFFT comparator --
 def cufft_comparator(p, q, steps: int = 20, warmup: int = 3):
     """The same convolution with cuFFT (torch.fft) on the full zero-padded grid and a
-    separate contraction: pad rho, R2C of every field, sigma^_c = sum_e i g_ce rho^_e
-    (FP32 imaginary-only spectra, as in our path; values are random -- timing only),
-    C2R of the six components, crop.  Returns ms per evaluation for the whole
-    comparator and for its FFTs alone (a lower bound for any cuFFT-based pipeline)."""
+    separate contraction kernel (dds_contract_spectra): pad rho, R2C of every field,
+    sigma^_c = sum_e i g_ce rho^_e (FP32 imaginary-only spectra, as in our path; values
+    are random -- timing only), C2R of the six components, crop.  Returns ms per
+    evaluation for the whole comparator and for its FFTs alone (a lower bound for any
+    cuFFT-based pipeline)."""
     import torch
+
+    import paper_1804_01830_gb300 as dds
     g = p.geom
     nz, ny, nx = g.nz, g.ny, g.nx
     pz, py, px = q["pz"], q["py"], q["px"]
@@ -232,28 +235,22 @@ def cufft_comparator(p, q, steps: int = 20, warmup: int = 3):
     rho = torch.rand((fe, nz, ny, nx), device=dev)
     pad = torch.zeros((fe, pz, py, px), device=dev)
     kx = px // 2 + 1
+    nk = pz * py * kx
     gspec = torch.rand((6, fe, pz, py, kx), device=dev)
     sig = torch.empty((6, nz, ny, nx), device=dev)
+    S = torch.empty((6, pz, py, kx), dtype=torch.complex64, device=dev)
 
     def full():
         pad[:, :nz, :ny, :nx].copy_(rho)
-        R = torch.fft.rfftn(pad, dim=(1, 2, 3))
-        Rr = torch.view_as_real(R)                      # (fe, pz, py, kx, 2)
-        S = torch.zeros((6, pz, py, kx), dtype=torch.complex64, device=dev)
-        Sr = torch.view_as_real(S)
-        for c in range(6):                              # sigma^_c = sum_e i g_ce rho^_e
-            for e in range(fe):
-                Sr[c, ..., 0].addcmul_(gspec[c, e], Rr[e, ..., 1], value=-1.0)
-                Sr[c, ..., 1].addcmul_(gspec[c, e], Rr[e, ..., 0])
+        R = torch.fft.rfftn(pad, dim=(1, 2, 3)).contiguous()
+        dds.dds_contract_spectra(R.data_ptr(), fe, gspec.data_ptr(), S.data_ptr(), nk)
         out = torch.fft.irfftn(S, s=(pz, py, px), dim=(1, 2, 3))
         sig.copy_(out[:, :nz, :ny, :nx])
-
-    spec_out = torch.empty((6, pz, py, kx), dtype=torch.complex64, device=dev)
 
     def fft_only():
         pad[:, :nz, :ny, :nx].copy_(rho)
         torch.fft.rfftn(pad, dim=(1, 2, 3))
-        out = torch.fft.irfftn(spec_out, s=(pz, py, px), dim=(1, 2, 3))
+        out = torch.fft.irfftn(S, s=(pz, py, px), dim=(1, 2, 3))
         sig.copy_(out[:, :nz, :ny, :nx])
 
     res = {}
@@ -268,9 +265,61 @@ def cufft_comparator(p, q, steps: int = 20, warmup: int = 3):
         b.record()
         torch.cuda.synchronize()
         res[name] = a.elapsed_time(b) / steps
-    del pad, gspec, rho, sig, spec_out
+    # the contraction kernel alone, and its bytes (read rho^ and g, write sigma^)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    R = torch.fft.rfftn(pad, dim=(1, 2, 3)).contiguous()
+    a.record()
+    for _ in range(steps):
+        dds.dds_contract_spectra(R.data_ptr(), fe, gspec.data_ptr(), S.data_ptr(), nk)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    cb = nk * (8 * fe + 4 * 6 * fe + 8 * 6)
+    res["contraction_kernel_ms"] = ms
+    res["contraction_kernel_gbs"] = cb / (ms * 1e-3) / 1e9
+    del pad, gspec, rho, sig, S, R
     torch.cuda.empty_cache()
     return res
+
+
+def padded_sizes(nx: int, ny: int, nz: int):
+    """The library's zero-padded FFT sizes for a grid (next power of two >= 2n, at least
+    32 in x and y and 16 in z)."""
+    p2 = lambda n: 1 << (2 * n - 1).bit_length()
+    return max(32, p2(nx)), max(32, p2(ny)), max(16, p2(nz))
+
+
+def cpu_fft_baseline(nx: int, ny: int, nz: int, fe: int, note: str = ""):
+    """The same zero-padded FFT convolution in FP64 with PyTorch's CPU FFT on the host
+    cores (R2C of every field, contraction with imaginary-only kernel spectra, C2R of the
+    six components, crop): the O(N log N) CPU route of Sec. 2.3.  Spectra values are
+    random (timing only).  One evaluation after one warm-up; returns cells/s."""
+    import torch
+    px, py, pz = padded_sizes(nx, ny, nz)
+    kx = px // 2 + 1
+    gen = torch.Generator().manual_seed(0)
+    rho = torch.rand((fe, nz, ny, nx), dtype=torch.float64, generator=gen)
+    gs = torch.rand((6, fe, pz, py, kx), dtype=torch.float64, generator=gen)
+
+    def once():
+        R = torch.fft.rfftn(rho, s=(pz, py, px), dim=(1, 2, 3))
+        out = torch.empty((6, nz, ny, nx), dtype=torch.float64)
+        for c in range(6):
+            S = torch.zeros((pz, py, kx), dtype=torch.complex128)
+            for e in range(fe):
+                S.add_(R[e] * (1j * gs[c, e]))
+            out[c] = torch.fft.irfftn(S, s=(pz, py, px))[:nz, :ny, :nx]
+        return out
+
+    once()
+    t0 = time.perf_counter()
+    once()
+    dt = time.perf_counter() - t0
+    n = nx * ny * nz
+    return {"value": n / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "torch-cpu-fft-fp64",
+            "seconds_per_evaluation": dt,
+            "sample": f"one evaluation of a {nx}x{ny}x{nz} grid ({fe} fields, padded {px}x{py}x{pz}) after one "
+                      f"warm-up{note}"}
 
 
 # ----------------------------------------------------------------- serving --
@@ -462,37 +511,45 @@ def sweep_benchmark(device: int, n_real: int = 64, reps: int = 5, oracle_targets
 
 
 def serving_benchmark(device: int, duration: float, rate: float = 200.0, budget: float = 150e9, seed: int = 0,
-                      n_streams: int = 4, max_batch: int = 2):
-    """Poisson stream of stress requests (mixed grids, cell aspects and family sets)
-    through the continuous-batching server; kernel spectra cached per geometry (warmed
-    before the timed stream), admission by an HBM budget.  Latency = submission to the
-    stress array on the host."""
+                      n_streams: int = 4, max_batch: int = 2, pool: int = 3):
+    """Poisson stream of stress requests through the continuous-batching server: per
+    request a grid, a cell aspect, 1-4 of the 18 GaN families and a grain seed.  One
+    context of all 18 families per geometry (its kernel spectra cached on the device,
+    built before the timed stream) serves every family subset; admission by an HBM
+    budget.  The densities are made before the stream: `pool` grain realisations per
+    geometry, a request's seed choosing one (making a 512x512 realisation takes about half a
+    second, too slow to do per request at 200/s).  Latency = submission to the stress
+    array on the host, with its parts (queue, copies, device) per request."""
     import torch
 
     from paper_1804_01830_gb300.serve import StressRequest, StressServer
     arrivals = W.serving_stream(seed, duration, rate)
-    kinds = sorted({(gi, ai, fi) for _, gi, ai, fi in arrivals})
-    dens = {}
-    cases = {}
-    for gi, ai, fi in kinds:
-        c = W.serving_problem(gi, ai, fi, seed=seed)
-        if (gi, fi) not in dens:
-            dens[(gi, fi)] = torch.from_numpy(c.rho).pin_memory()
-        cases[(gi, ai, fi)] = c
+    geoms = sorted({(a.grid, a.aspect) for a in arrivals})
+    t_make = time.perf_counter()
+    slots = {}
+    for gi, ai in geoms:
+        for s in range(pool):
+            slots[(gi, ai, s)] = torch.from_numpy(W.serving_slots(gi, ai, 7919 * s + 1)).pin_memory()
+    t_make = time.perf_counter() - t_make
+    t18, b18 = W.gan_families()
 
-    def request(kind):
-        c = cases[kind]
-        g = c.geom
-        return StressRequest((g.nx, g.ny, g.nz), (g.dx, g.dy, g.dz), g.mu, g.nu, c.t, c.b, dens[(kind[0], kind[2])])
+    def request(a):
+        g = W.serving_geometry(a.grid, a.aspect)
+        rho = slots[(a.grid, a.aspect, a.seed % pool)][: len(a.fam)]
+        return StressRequest((g.nx, g.ny, g.nz), (g.dx, g.dy, g.dz), g.mu, g.nu, t18, b18, rho, fam=a.fam)
 
     srv = StressServer(device=device, hbm_budget=budget, n_streams=n_streams, max_batch=max_batch)
     t0 = time.perf_counter()
-    for kind in kinds:
-        srv.warm(request(kind))
+    first = {}
+    for a in arrivals:
+        first.setdefault((a.grid, a.aspect), a)
+    for a in first.values():                       # build every geometry's context, 4-family buffers
+        srv.warm(request(W.ServingArrival(0.0, a.grid, a.aspect, (0, 1, 2, 3), 0)))
     build_s = time.perf_counter() - t0
-    for kind in kinds:                     # untimed: one request per kind primes pinned buffers
-        srv.submit(request(kind)).result(timeout=600)
+    for a in first.values():                       # untimed: one request per geometry primes the buffers
+        srv.submit(request(a)).result(timeout=600)
     srv.latencies.clear()
+    srv.records.clear()
 
     done = threading.Semaphore(0)
     errors = []
@@ -503,26 +560,38 @@ def serving_benchmark(device: int, duration: float, rate: float = 200.0, budget:
         done.release()
 
     cells = 0
+    late = 0
     t0 = time.perf_counter()
-    for ta, gi, ai, fi in arrivals:
-        dt = ta - (time.perf_counter() - t0)
+    for a in arrivals:
+        dt = a.time - (time.perf_counter() - t0)
         if dt > 0:
             time.sleep(dt)
-        srv.submit(request((gi, ai, fi))).add_done_callback(finished)
-        cells += cases[(gi, ai, fi)].geom.n_cells
+        elif dt < -0.005:
+            late += 1
+        srv.submit(request(a)).add_done_callback(finished)
+        cells += int(np.prod(W.SERVING_GRIDS[a.grid]))
     for _ in arrivals:
         if not done.acquire(timeout=600):
             raise RuntimeError("serving benchmark timed out")
     wall = time.perf_counter() - t0
     lat = srv.latency_ms()
+    br = srv.breakdown_ms()
+    dev = np.array([r["device_ms"] for r in srv.records])
+    big = [r["device_ms"] for r in srv.records if r["cells"] == max(int(np.prod(g)) for g in W.SERVING_GRIDS)]
+    ctxs = len(srv.cache)
     srv.close()
     if errors:
         raise errors[0]
     return {"arrivals": f"Poisson {rate:g}/s for {duration:g} s", "requests": len(arrivals),
             "grids": [list(gr) for gr in W.SERVING_GRIDS], "dz_over_dx": W.SERVING_ASPECTS,
-            "family_sets": W.SERVING_FAMILY_SETS, "contexts": len(kinds), "kernel_build_s": build_s,
+            "families_per_request": "1-4 of the 18 GaN families, uniform", "grain_realisations_per_geometry": pool,
+            "contexts": ctxs, "kernel_build_s": build_s, "density_setup_s": t_make,
             "p50_ms": lat.get("p50"), "p99_ms": lat.get("p99"), "mean_ms": lat.get("mean"),
-            "max_ms": lat.get("max"), "throughput_req_per_s": len(arrivals) / wall,
+            "max_ms": lat.get("max"), "breakdown_ms": br,
+            "slowest_request_device_ms": float(dev.max()) if dev.size else None,
+            "largest_grid_device_ms_p50": float(np.percentile(big, 50)) if big else None,
+            "submissions_late_by_over_5ms": late,
+            "throughput_req_per_s": len(arrivals) / wall,
             "cells_per_s": cells / wall, "hbm_budget_gb": budget / 1e9, "streams": n_streams,
             "max_batch": max_batch}
 
@@ -724,6 +793,15 @@ def run_ours(args):
                "sample": f"{n} random target cells of {args.workload}, FP64 direct sum of Eq. 10 over all "
                          f"{g.n_cells} source cells x {p.n_families} families ({dt:.1f} s)"}
 
+    cpu_fft = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sx, sy, note = g.nx, g.ny, ""
+        while sx * sy * g.nz > 2_500_000 and sx > 32:     # bounded sample: halve x and y
+            sx, sy = sx // 2, sy // 2
+        if (sx, sy) != (g.nx, g.ny):
+            note = f"; the workload's grid with x and y halved to bound the run (FFT work per cell grows as log N)"
+        cpu_fft = cpu_fft_baseline(sx, sy, g.nz, q["n_fields"], note)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -747,6 +825,7 @@ def run_ours(args):
         "grain_size_scaling": grain,
         "batched_sweep": sweep,
         "cpu_baseline": cpu,
+        "cpu_fft_baseline": cpu_fft,
         "gpu_launches": K * ctx.launches_per_stress,
         "clocks": clk,
     }

@@ -210,6 +210,18 @@ void dds_graph_destroy(dds_graph *graph);
  * needed.  Enqueued on `cuda_stream`; returns without synchronising. */
 int dds_stress_noalloc(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, void *cuda_stream);
 
+/* Evaluation for a subset of the context's families.  Eq. 3b sums the stress over the
+ * families present, and the coefficients are linear in b (Sec. 2.1), so one built
+ * context -- one set of kernel spectra per geometry (Sec. 2.3) -- serves any subset of
+ * its families: rho holds only the n families fam[0..n-1] (distinct indices into the
+ * families given to dds_set_families), the others count as zero density.  rho: device,
+ * [nb][n][nz][ny][nx] (F32 or BF16); sigma: device, [nb][6][nz][ny][nx] FP32; fam: host.
+ * 1 <= nb <= 4096, 1 <= n <= F.  The result equals dds_stress_multi with the absent
+ * families' densities set to zero (same arithmetic, fewer density reads).  Errors:
+ * INVALID_ARG (bad index, repeated index, sizes, alignment), NOT_READY, OOM, CUDA. */
+int dds_stress_subset(dds_ctx *ctx, int nb, int n, const int *fam, const void *rho, int rho_dtype, float *sigma,
+                      void *cuda_stream);
+
 /* End-to-end variant with HOST buffers: copies rho_host (float32, [F][nz][ny][nx])
  * to the device, evaluates, copies sigma back to sigma_host (float32,
  * [6][nz][ny][nx]) and synchronises the stream.  Device staging buffers are owned
@@ -233,6 +245,24 @@ int dds_query(const dds_ctx *ctx, int *n_fields, int *px, int *py, int *pz);
  * straight-dislocation field), only the spectra of ky <= py/2 are stored.  *bytes
  * receives the size.  Errors: INVALID_ARG (NULL), NOT_READY (not built). */
 int dds_spectra_bytes(const dds_ctx *ctx, unsigned long long *bytes);
+
+/* Device bytes that dds_build_kernels will hold for this geometry and family set --
+ * the kernel spectra (the per-geometry coefficients of Sec. 2.3, in Fourier space) and
+ * the work buffers for nb density sets -- computed from the plan without allocating
+ * (set geometry and families first).  For admission control before a build.  Errors:
+ * INVALID_ARG, NOT_READY, UNSUPPORTED (no z-pass schedule for the grid). */
+int dds_footprint(dds_ctx *ctx, int nb, unsigned long long *bytes);
+
+/* The contraction of Eq. 10 in Fourier space (Sec. 2.3: the convolution becomes a
+ * product of spectra, summed over the fields as in Eq. 3b) as a separate kernel, for
+ * timing a library-FFT pipeline against the fused passes; dds_stress never calls it.
+ *   sigma_hat[c][k] = sum_e (i g[c][e][k]) rho_hat[e][k],  c < 6, e < fe, k < nk.
+ * rho_hat: device, complex FP32 (interleaved re, im), [fe][nk]; g: device, FP32 real
+ * (the imaginary parts of purely imaginary kernel spectra), [6][fe][nk]; sigma_hat:
+ * device, complex FP32, [6][nk], written.  1 <= fe <= 8.  Needs no context; enqueued
+ * on cuda_stream.  Errors: INVALID_ARG, CUDA. */
+int dds_contract_spectra(const void *rho_hat, int fe, const float *g, void *sigma_hat, long long nk,
+                         void *cuda_stream);
 
 /* Number of kernel launches one dds_stress call issues. */
 int dds_launches_per_stress(const dds_ctx *ctx);

@@ -34,9 +34,9 @@ DDS_OPT_PBC_SHELLS = 4
 # Every symbol include/dds.h declares.
 EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option", "dds_autotune",
            "dds_build_kernels", "dds_stress", "dds_stress_multi", "dds_stress_stats", "dds_stress_batched",
-           "dds_stress_noalloc",
+           "dds_stress_noalloc", "dds_stress_subset",
            "dds_stress_host",
-           "dds_table_at", "dds_query", "dds_spectra_bytes", "dds_launches_per_stress", "dds_profile_enable",
+           "dds_table_at", "dds_query", "dds_footprint", "dds_spectra_bytes", "dds_contract_spectra", "dds_launches_per_stress", "dds_profile_enable",
            "dds_profile_read", "dds_relax", "dds_graph_capture", "dds_graph_launch", "dds_graph_nodes",
            "dds_graph_destroy", "dds_device_status", "dds_last_error", "dds_destroy")
 
@@ -72,12 +72,15 @@ def load_library():
         "dds_stress_batched": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), ip,
                                 ctypes.POINTER(vp), vp], ctypes.c_int),
         "dds_stress_noalloc": ([vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "dds_stress_subset": ([vp, ctypes.c_int, ctypes.c_int, ip, vp, ctypes.c_int, vp, vp], ctypes.c_int),
         "dds_stress_multi": ([vp, ctypes.c_int, vp, ctypes.c_int, vp, vp], ctypes.c_int),
         "dds_stress_stats": ([vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
         "dds_stress_host": ([vp, vp, vp, vp], ctypes.c_int),
         "dds_table_at": ([vp, dp, dp, lp, ip, dp], ctypes.c_int),
         "dds_query": ([vp, ip, ip, ip, ip], ctypes.c_int),
         "dds_spectra_bytes": ([vp, ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
+        "dds_footprint": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
+        "dds_contract_spectra": ([vp, ctypes.c_int, vp, vp, ctypes.c_longlong, vp], ctypes.c_int),
         "dds_launches_per_stress": ([vp], ctypes.c_int),
         "dds_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
         "dds_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ip, ip], ctypes.c_int),
@@ -161,6 +164,14 @@ def dds_stress_multi(ctx, nb: int, rho_ptr: int, rho_dtype: int, sigma_ptr: int,
                                                 ctypes.c_void_p(sigma_ptr), _stream_handle(stream)))
 
 
+def dds_stress_subset(ctx, nb: int, fam, rho_ptr: int, rho_dtype: int, sigma_ptr: int, stream=None):
+    fam = [int(f) for f in fam]
+    arr = (ctypes.c_int * len(fam))(*fam)
+    _check(ctx, load_library().dds_stress_subset(ctx, int(nb), len(fam), arr, ctypes.c_void_p(rho_ptr),
+                                                 int(rho_dtype), ctypes.c_void_p(sigma_ptr),
+                                                 _stream_handle(stream)))
+
+
 def dds_stress_stats(ctx, nb: int, rho_ptr: int, rho_dtype: int, sigma_ptr: int, s_ptr: int, stream=None):
     _check(ctx, load_library().dds_stress_stats(ctx, int(nb), ctypes.c_void_p(rho_ptr), int(rho_dtype),
                                                 ctypes.c_void_p(sigma_ptr), ctypes.c_void_p(s_ptr),
@@ -213,10 +224,22 @@ def dds_query(ctx):
             "spectra_bytes": dds_spectra_bytes(ctx)}
 
 
+def dds_footprint(ctx, nb: int = 1) -> int:
+    b = ctypes.c_ulonglong()
+    _check(ctx, load_library().dds_footprint(ctx, int(nb), ctypes.byref(b)))
+    return int(b.value)
+
+
 def dds_spectra_bytes(ctx) -> int:
     b = ctypes.c_ulonglong()
     _check(ctx, load_library().dds_spectra_bytes(ctx, ctypes.byref(b)))
     return int(b.value)
+
+
+def dds_contract_spectra(rho_hat_ptr: int, fe: int, g_ptr: int, sigma_hat_ptr: int, nk: int, stream=None):
+    _check(None, load_library().dds_contract_spectra(ctypes.c_void_p(rho_hat_ptr), int(fe), ctypes.c_void_p(g_ptr),
+                                                     ctypes.c_void_p(sigma_hat_ptr), int(nk),
+                                                     _stream_handle(stream)))
 
 
 def dds_launches_per_stress(ctx) -> int:
@@ -398,6 +421,30 @@ class StressContext:
             sigma = torch.empty((nb, 6) + self.shape, dtype=torch.float32, device=rho.device)
         dds_stress_multi(self.handle, nb, rho.data_ptr(), dt, sigma.data_ptr(), stream)
         return sigma
+
+    def footprint(self, nb: int = 1) -> int:
+        """Device bytes a build will hold (spectra + work buffers for nb sets), before building."""
+        return dds_footprint(self.handle, nb)
+
+    def stress_subset(self, fam, rho, sigma=None, stream=None):
+        """Only the families `fam` (indices into this context's families) carry density:
+        rho CUDA tensor (len(fam), nz, ny, nx) or (nb, len(fam), nz, ny, nx) -> sigma
+        (6, nz, ny, nx) or (nb, 6, nz, ny, nx); the other families count as zero."""
+        import torch
+        batched = rho.dim() == 5
+        r = rho if batched else rho.unsqueeze(0)
+        if not r.is_cuda or not r.is_contiguous():
+            raise ValueError("rho must be a contiguous CUDA tensor")
+        if tuple(r.shape[1:]) != (len(fam),) + self.shape:
+            raise ValueError(f"rho has shape {tuple(rho.shape)}")
+        dt = {torch.float32: DDS_F32, torch.bfloat16: DDS_BF16}.get(r.dtype)
+        if dt is None:
+            raise ValueError(f"unsupported density dtype {r.dtype}")
+        nb = int(r.shape[0])
+        if sigma is None:
+            sigma = torch.empty((nb, 6) + self.shape, dtype=torch.float32, device=r.device)
+        dds_stress_subset(self.handle, nb, fam, r.data_ptr(), dt, sigma.data_ptr(), stream)
+        return sigma if batched else sigma[0]
 
     def stress_stats(self, rho, sigma=None, stream=None):
         """sigma and the Eq. 20 in-plane RMS per component and height: returns (sigma, s)

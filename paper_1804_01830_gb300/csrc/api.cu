@@ -652,6 +652,57 @@ int dds_stress_multi(dds_ctx *ctx, int nb, const void *rho, int rho_dtype, float
   return enqueue_stress(ctx, rho, rho_dtype, sigma, s, nb);
 }
 
+int dds_stress_subset(dds_ctx *ctx, int nb, int n, const int *fam, const void *rho, int rho_dtype, float *sigma,
+                      void *cuda_stream) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!ctx->built) return fail(ctx, DDS_ERR_NOT_READY, "stress_subset: call dds_build_kernels first");
+  if (nb < 1 || nb > 4096) return fail(ctx, DDS_ERR_INVALID_ARG, "stress_subset: nb = %d outside [1, 4096]", nb);
+  if (!fam || !rho || !sigma) return fail(ctx, DDS_ERR_INVALID_ARG, "stress_subset: NULL pointer");
+  if (n < 1 || n > ctx->F)
+    return fail(ctx, DDS_ERR_INVALID_ARG, "stress_subset: n = %d outside [1, %d]", n, ctx->F);
+  if (rho_dtype != DDS_F32 && rho_dtype != DDS_BF16)
+    return fail(ctx, DDS_ERR_INVALID_ARG, "stress_subset: unknown density type %d", rho_dtype);
+  if (((uintptr_t)rho & 15) || ((uintptr_t)sigma & 15))
+    return fail(ctx, DDS_ERR_INVALID_ARG, "stress_subset: rho and sigma must be 16-byte aligned");
+  std::vector<int> slot(ctx->F, -1);      // family -> its position in rho
+  for (int i = 0; i < n; ++i) {
+    if (fam[i] < 0 || fam[i] >= ctx->F || slot[fam[i]] >= 0)
+      return fail(ctx, DDS_ERR_INVALID_ARG, "stress_subset: family index %d out of range or repeated", fam[i]);
+    slot[fam[i]] = i;
+  }
+  // the context's collapse restricted to the given families (fields and coefficients
+  // unchanged; a group without any of them contributes zero fields)
+  Collapse sub = ctx->col;
+  int pos = 0;
+  for (int g = 0; g < ctx->col.ngroups; ++g) {
+    const int f0 = pos;
+    for (int q = 0; q < ctx->col.nf[g]; ++q) {
+      const int src = ctx->col.f0[g] + q, i = slot[ctx->col.fam[src]];
+      if (i < 0) continue;
+      sub.fam[pos] = i;
+      for (int d = 0; d < 3; ++d) sub.coef[pos][d] = ctx->col.coef[src][d];
+      ++pos;
+    }
+    sub.f0[g] = f0;
+    sub.nf[g] = pos - f0;
+  }
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "cannot make device %d current", ctx->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (ctx->fe == 0) {
+    const cudaError_t err =
+        cudaMemsetAsync(sigma, 0, sizeof(float) * 6 * (size_t)nb * ctx->nx * ctx->ny * ctx->nz, s);
+    return err == cudaSuccess ? DDS_OK : fail(ctx, DDS_ERR_CUDA, "stress_subset: %s", cudaGetErrorString(err));
+  }
+  if (nb > ctx->nb_cap) {
+    const cudaError_t err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress_subset: %s", cudaGetErrorString(err));
+    const int rc = alloc_work(ctx, nb);
+    if (rc != DDS_OK) return rc;
+  }
+  return enqueue_stress(ctx, rho, rho_dtype, sigma, s, nb, nullptr, nullptr, &sub, n);
+}
+
 int dds_stress_stats(dds_ctx *ctx, int nb, const void *rho, int rho_dtype, float *sigma, float *s_out,
                      void *cuda_stream) {
   if (!ctx) return DDS_ERR_INVALID_ARG;
@@ -891,6 +942,27 @@ int dds_query(const dds_ctx *ctx, int *n_fields, int *px, int *py, int *pz) {
   if (px) *px = 2 * ctx->shape.M;
   if (py) *py = ctx->shape.py;
   if (pz) *pz = ctx->shape.pz;
+  return DDS_OK;
+}
+
+int dds_footprint(dds_ctx *ctx, int nb, unsigned long long *bytes) {
+  if (!ctx || !bytes) return DDS_ERR_INVALID_ARG;
+  if (nb < 1 || nb > 4096) return fail(ctx, DDS_ERR_INVALID_ARG, "footprint: nb = %d outside [1, 4096]", nb);
+  if (!ctx->has_geom || !ctx->has_fam) return fail(ctx, DDS_ERR_NOT_READY, "footprint: set geometry and families first");
+  const Shape saved = ctx->shape;
+  const int rc = make_plan(ctx);            // host-only; restored below
+  const Shape sh = ctx->shape;
+  ctx->shape = saved;
+  if (rc != DDS_OK) return rc;
+  const size_t fe = (size_t)std::max(sh.fe, 1);
+  size_t ks = (size_t)sh.py * (sh.M + 1) * sh.pz * 6 * fe;
+  if (sh.zfour) {
+    Shape tmp = sh;
+    ks = zfour_symmetry(ctx->field_t.data(), ctx->field_b.data(), sh.fe, &tmp);
+  }
+  size_t a, b, na, nbuf;
+  work_sizes(sh, nb, &a, &b, &na, &nbuf);
+  *bytes = (unsigned long long)(ks * (ctx->spectra_fp16 ? 2 : 4) + (a + b + na + nbuf) * sizeof(float2));
   return DDS_OK;
 }
 

@@ -153,8 +153,11 @@ CoefGeom make_coef_geom(const dds_ctx *ctx);
 int build_spectra(dds_ctx *ctx, cudaStream_t s);
 
 // Enqueue one stress evaluation.
+// sub: a restricted family collapse whose family indices point into rho's sub_fin
+// families (dds_stress_subset); default: the context's own.
 int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s, int nb = 1,
-                   double *stats = nullptr, float *s_out = nullptr);
+                   double *stats = nullptr, float *s_out = nullptr, const Collapse *sub = nullptr,
+                   int sub_fin = 0);
 int stress_launch_count(const Shape &sh, const Collapse &col);
 
 // Free-surface relaxation (Sec. 5): n_steps explicit steps on u, then sigma_tot.

@@ -293,9 +293,11 @@ int stress_launch_count(const Shape &sh, const Collapse &col) {
 }
 
 int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s, int nb,
-                   double *stats, float *s_out) {
+                   double *stats, float *s_out, const Collapse *sub, int sub_fin) {
   Shape sh = ctx->shape;
   sh.nb = nb;
+  if (sub) sh.fin = sub_fin;
+  const Collapse &col = sub ? *sub : ctx->col;
   const float2 *tw = ctx->tw.f32;
   cudaEvent_t *ev = nullptr;
   cudaError_t err = cudaSuccess;
@@ -315,7 +317,7 @@ int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, c
   auto mark = [&](int i) {
     if (ev && err == cudaSuccess) err = cudaEventRecord(ev[i], s);
   };
-  if (err == cudaSuccess) err = dispatch_x_fwd(sh, ctx->col, rho, rho_dtype == DDS_BF16, ctx->bufA, ctx->nyqA, tw, s);
+  if (err == cudaSuccess) err = dispatch_x_fwd(sh, col, rho, rho_dtype == DDS_BF16, ctx->bufA, ctx->nyqA, tw, s);
   mark(1);
   if (err == cudaSuccess) err = dispatch_y<false>(sh, nb * sh.fe, ctx->bufA, ctx->nyqA, ctx->bufB, ctx->nyqB, tw, s);
   mark(2);

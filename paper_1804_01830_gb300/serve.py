@@ -3,17 +3,22 @@
 Requests (grid geometry, dislocation families, densities) arrive at any time from
 any thread.  A scheduler thread
 
-  * keeps one built context per (geometry, families) in a cache, so the kernel
+  * keeps one built context per (geometry, family set) in a cache, so the kernel
     spectra of a geometry stay resident in HBM and are built once (Sec. 2.3: the
-    coefficients are computed once per geometry); idle contexts are evicted, least
-    recently used first, when the HBM budget needs room;
-  * admits a request when its device footprint (the context, if not yet resident,
-    plus the request's density and stress buffers) fits the budget;
-  * evaluates the waiting requests of one context together (one dds_stress_multi
+    coefficients are computed once per geometry).  A request may carry densities for
+    a subset of the context's families only (``fam``): Eq. 3b sums over the families
+    present and the coefficients are linear in b, so one context per geometry serves
+    every subset (dds_stress_subset).  Idle contexts are evicted, least recently used
+    first, when the HBM budget needs room;
+  * admits a request when its device footprint fits the budget: the context (computed
+    from its plan before it is built, dds_footprint) if not yet resident, plus the
+    request's density and stress buffers;
+  * evaluates the waiting requests of one context and family subset together (one
     call, the spectra read once), and runs different contexts on different CUDA
     streams, so work admitted while other work is on the GPU overlaps with it;
-  * returns results through futures and records each request's latency
-    (submission to result on the host).
+  * returns results through futures and records, per request, the latency (submission
+    to result on the host) and its parts: queueing before launch, host-to-device copy,
+    device evaluation and device-to-host copy (CUDA events on the request's stream).
 
 A context has one set of work buffers, so at most one evaluation per context is in
 flight; requests for a busy context wait while other contexts proceed.
@@ -38,9 +43,10 @@ class StressRequest:
     cells: tuple           # (dx, dy, dz) in m
     mu: float
     nu: float
-    t: np.ndarray          # (F, 3)
+    t: np.ndarray          # (F, 3): the family set of the context
     b: np.ndarray          # (F, 3)
-    rho: object            # (F, nz, ny, nx) float32: torch tensor (pinned host or device) or numpy
+    rho: object            # (n, nz, ny, nx) float32: torch tensor (pinned host or device) or numpy
+    fam: tuple = None      # indices into (t, b) of rho's n families; None: all F, in order
     submitted: float = field(default=0.0)
 
     def key(self):
@@ -52,23 +58,25 @@ class StressRequest:
             self.__dict__["_key"] = k
         return k
 
+    def batch_key(self):
+        """Requests evaluated in one call: same context and same family subset."""
+        return (self.key(), None if self.fam is None else tuple(int(f) for f in self.fam))
+
+    def n_rho(self) -> int:
+        return len(self.t) if self.fam is None else len(self.fam)
+
 
 class _Entry:
-    def __init__(self, ctx: StressContext, nbytes: int):
+    def __init__(self, ctx, nbytes: int):
         self.ctx = ctx
         self.nbytes = nbytes
         self.busy = False
 
 
-def context_bytes(q: dict, grid, n_families: int, nb: int = 1) -> int:
-    """Device bytes of a built context: FP32 kernel spectra plus work buffers for nb sets."""
+def io_buffer_bytes(grid, n_rho: int, nb: int = 1) -> int:
+    """Device bytes of one launch's density and stress buffers for nb requests."""
     nx, ny, nz = grid
-    fe, px, py, pz = q["n_fields"], q["px"], q["py"], q["pz"]
-    m = px // 2
-    spectra = 6 * max(fe, 1) * py * (m + 1) * pz * 4
-    a = max(fe * nz * ny * m, 6 * nz * py * m) * nb
-    b = max(fe * nz * py * m, 6 * nz * ny * m) * nb
-    return spectra + (a + b) * 8 + (2 << 20)
+    return 4 * nx * ny * nz * (n_rho + 6) * nb
 
 
 class CudaBackend:
@@ -84,19 +92,36 @@ class CudaBackend:
         self.max_batch = max_batch
         self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
 
-    def build(self, req: StressRequest):
-        """A built context for the request's geometry and families, and its device bytes."""
-        torch = self.torch
+    def _context(self, req: StressRequest):
         ctx = StressContext(self.device)
         nx, ny, nz = req.grid
         dx, dy, dz = req.cells
         ctx.set_geometry(nx, ny, nz, dx, dy, dz, req.mu, req.nu).set_families(req.t, req.b)
+        return ctx
+
+    def footprint(self, req: StressRequest) -> int:
+        """Device bytes the request's context will hold once built (spectra, work buffers
+        for a full batch, and the per-stream density and stress buffers that build()
+        leaves cached), computed before building."""
+        ctx = self._context(req)
+        try:
+            lib = ctx.footprint(self.max_batch)
+        finally:
+            ctx.close()
+        return lib + len(self.streams) * io_buffer_bytes(req.grid, req.n_rho(), self.max_batch) + (2 << 20)
+
+    def build(self, req: StressRequest):
+        """A built context for the request's geometry and families, and its device bytes."""
+        torch = self.torch
+        ctx = self._context(req)
         ctx.build_kernels(self.streams[0])
+        nx, ny, nz = req.grid
+        n = req.n_rho()
         if self.max_batch > 1:
             # size the work buffers for a full batch now (growing them later synchronises the device)
             with torch.cuda.stream(self.streams[0]):
-                z = torch.zeros((self.max_batch, len(req.t), nz, ny, nx), device=f"cuda:{self.device}")
-                ctx.stress_multi(z, stream=self.streams[0])
+                z = torch.zeros((self.max_batch, 1, nz, ny, nx), device=f"cuda:{self.device}")
+                ctx.stress_subset([0], z, stream=self.streams[0])
             self.streams[0].synchronize()
             del z
         # buffers for as many batches as there are streams -- pinned host results, and on
@@ -108,36 +133,55 @@ class CudaBackend:
                 for _ in range(len(self.streams))]
         for st in self.streams:
             with torch.cuda.stream(st):
-                keep.append(torch.empty((self.max_batch, len(req.t), nz, ny, nx), dtype=torch.float32, device=dev))
+                keep.append(torch.empty((self.max_batch, n, nz, ny, nx), dtype=torch.float32, device=dev))
                 keep.append(torch.empty((self.max_batch, 6, nz, ny, nx), dtype=torch.float32, device=dev))
         del keep
-        return ctx, context_bytes(ctx.query(), req.grid, len(req.t), self.max_batch)
+        return ctx, self.footprint(req)
 
     def launch(self, ctx, reqs, stream):
-        """Enqueue one batch on `stream`: densities in, stress_multi, results to pinned host
-        memory.  Returns a job handle for ready() / results()."""
+        """Enqueue one batch on `stream`: densities in, evaluation, results to pinned host
+        memory, with CUDA events between the steps.  Returns a job handle for ready() /
+        results() / timings()."""
         torch = self.torch
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         with torch.cuda.stream(stream):
+            ev[0].record(stream)
             rho = torch.empty((len(reqs),) + tuple(reqs[0].rho.shape), dtype=torch.float32,
                               device=f"cuda:{self.device}")
             for i, r in enumerate(reqs):
                 rho[i].copy_(r.rho, non_blocking=True)
-            sigma = ctx.stress_multi(rho, stream=stream)
+            ev[1].record(stream)
+            if reqs[0].fam is None:
+                sigma = ctx.stress_multi(rho, stream=stream)
+            else:
+                sigma = ctx.stress_subset(reqs[0].fam, rho, stream=stream)
+            ev[2].record(stream)
             out = torch.empty(sigma.shape, dtype=sigma.dtype, pin_memory=True)
             out.copy_(sigma, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(stream)
-        return {"event": ev, "keep": (rho, sigma), "out": out}
+            ev[3].record(stream)
+        return {"events": ev, "keep": (rho, sigma), "out": out}
 
     @staticmethod
     def ready(job) -> bool:
-        return job["event"].query()
+        return job["events"][3].query()
 
     @staticmethod
     def results(job):
         """Per request of the batch, sigma (6, nz, ny, nx) as a view of the pinned buffer."""
         out = job["out"].numpy()
         return [out[i] for i in range(out.shape[0])]
+
+    @staticmethod
+    def timings(job):
+        """(h2d, device, d2h) milliseconds of a finished job."""
+        e = job["events"]
+        return e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])
+
+    @staticmethod
+    def interval(job, ref):
+        """(start, end) of the job's evaluation kernels in ms after event `ref`."""
+        e = job["events"]
+        return ref.elapsed_time(e[1]), ref.elapsed_time(e[2])
 
     def pin(self, rho: np.ndarray):
         return self.torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float32)).pin_memory()
@@ -162,6 +206,9 @@ class StressServer:
         self.inflight: list = []           # dicts: job, stream, entry, items, io
         self.inbox: "queue.Queue" = queue.Queue()
         self.latencies: list = []
+        self.records: list = []            # per request: latency and its parts, seconds / ms
+        self.keep_jobs = False             # keep finished jobs (tests read their event intervals)
+        self.finished_jobs: list = []
         self.stop_flag = False
         self.error = None
         self.thread = threading.Thread(target=self._run, name="stress-scheduler", daemon=True)
@@ -214,6 +261,10 @@ class StressServer:
         self.resident += e.nbytes
         return e
 
+    def _footprint(self, req: StressRequest) -> int:
+        fp = getattr(self.backend, "footprint", None)
+        return int(fp(req)) if fp is not None else 0
+
     def _make_room(self, need: float, keep=None) -> bool:
         """Evict idle contexts other than `keep`, least recently used first, until `need`
         more bytes fit."""
@@ -226,11 +277,11 @@ class StressServer:
             self.backend.close_context(e.ctx)
         return True
 
-    def _fit(self, group, keep):
-        """The longest prefix of `group` whose buffers fit the budget once idle contexts
-        other than `keep` are evicted."""
+    def _fit(self, group, keep, extra: float = 0.0):
+        """The longest prefix of `group` whose buffers (plus `extra` bytes) fit the budget
+        once idle contexts other than `keep` are evicted."""
         n = len(group)
-        while n > 0 and not self._make_room(self._io_bytes([r for r, _ in group[:n]]), keep):
+        while n > 0 and not self._make_room(extra + self._io_bytes([r for r, _ in group[:n]]), keep):
             n -= 1
         return group[:n]
 
@@ -248,15 +299,17 @@ class StressServer:
 
     @staticmethod
     def _io_bytes(reqs):
-        return sum(4 * int(np.prod(tuple(r.rho.shape))) * (1 + 6 / max(len(r.t), 1)) for r in reqs)
+        return sum(io_buffer_bytes(r.grid, r.n_rho()) for r in reqs)
 
     def _launch(self, entry: _Entry, items):
         stream = self.free_streams.pop()
         reqs = [r for r, _ in items]
+        t_launch = time.perf_counter()
         job = self.backend.launch(entry.ctx, reqs, stream)
         entry.busy = True
         io = self._io_bytes(reqs)
-        self.inflight.append({"job": job, "stream": stream, "entry": entry, "items": items, "io": io})
+        self.inflight.append({"job": job, "stream": stream, "entry": entry, "items": items, "io": io,
+                              "launched": t_launch})
         self.resident += io
 
     def _complete(self):
@@ -270,9 +323,16 @@ class StressServer:
                 job["entry"].busy = False
                 self.free_streams.append(job["stream"])
                 self.resident -= job["io"]
+                tm = getattr(self.backend, "timings", None)
+                parts = tm(job["job"]) if tm is not None else (0.0, 0.0, 0.0)
                 for (r, fut), sig in zip(job["items"], res):
                     self.latencies.append(now - r.submitted)
+                    self.records.append({"latency_s": now - r.submitted, "queue_s": job["launched"] - r.submitted,
+                                         "h2d_ms": parts[0], "device_ms": parts[1], "d2h_ms": parts[2],
+                                         "batch": len(job["items"]), "cells": int(np.prod(r.grid))})
                     fut.set_result(sig)
+                if self.keep_jobs:
+                    self.finished_jobs.append(job)
             else:
                 still.append(job)
         self.inflight = still
@@ -286,16 +346,24 @@ class StressServer:
                 if entry is not None and entry.busy:
                     continue                       # its context is on the GPU; try others
                 k = req.key()
-                group = [(r, f) for r, f in self.pending if r.key() == k][: self.max_batch]
-                if entry is None and self._fit(group, None):
-                    # a new context's own footprint is known once it is built: room for the
-                    # buffers first, build (which accounts the context), then fit again below
+                bk = req.batch_key()
+                group = [(r, f) for r, f in self.pending if r.batch_key() == bk][: self.max_batch]
+                if entry is None:
+                    # room for the new context (its footprint comes from its plan) and the
+                    # buffers of at least the first request, then build
                     try:
-                        entry = self._build_entry(req)
-                    except Exception as ex:        # a context that cannot be built fails its requests only
+                        need = self._footprint(req)
+                    except Exception as ex:        # a geometry the library refuses fails its requests only
                         self._reject(k, ex)
                         progressed = True
                         break
+                    if self._fit(group, None, extra=need):
+                        try:
+                            entry = self._build_entry(req)
+                        except Exception as ex:    # a context that cannot be built fails its requests only
+                            self._reject(k, ex)
+                            progressed = True
+                            break
                 if entry is not None:
                     group = self._fit(group, k)
                 if entry is None or not group:
@@ -324,7 +392,8 @@ class StressServer:
                         _, req, done, err = msg
                         try:
                             if self._get_entry(req) is None:
-                                self._make_room(0)
+                                if not self._make_room(self._footprint(req)):
+                                    raise MemoryError(f"context does not fit the {self.budget:.3g}-byte HBM budget")
                                 self._build_entry(req)
                         except Exception as ex:
                             err.append(ex)
@@ -354,3 +423,20 @@ class StressServer:
             return {"n": 0}
         return {"n": int(lat.size), "p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                 "mean": float(lat.mean()), "max": float(lat.max())}
+
+    def breakdown_ms(self):
+        """p50 / p99 of each latency part over the recorded requests (queue: submission to
+        launch on the host; h2d, device, d2h: CUDA events on the request's stream; rest:
+        latency minus those, i.e. the host noticing completion and returning the result)."""
+        if not self.records:
+            return {}
+        q = np.array([r["queue_s"] for r in self.records]) * 1e3
+        h = np.array([r["h2d_ms"] for r in self.records])
+        d = np.array([r["device_ms"] for r in self.records])
+        o = np.array([r["d2h_ms"] for r in self.records])
+        lat = np.array([r["latency_s"] for r in self.records]) * 1e3
+        rest = lat - q - h - d - o
+        out = {}
+        for name, a in (("queue", q), ("h2d", h), ("device", d), ("d2h", o), ("rest", rest)):
+            out[name] = {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99))}
+        return out

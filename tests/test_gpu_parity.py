@@ -200,15 +200,21 @@ def test_sweep_realisation_sampled(dds, r):
     assert rel_l2_per_component(got16[:, t16], ref16).max() <= TOL_STRESS
 
 
-@pytest.mark.parametrize("kind", [(0, 0, 1), (1, 1, 0), (3, 2, 1)])
-def test_serving_kinds_sampled(dds, kind):
-    # request kinds of the serving mix: grid, cell aspect dz/dx, family set
-    c = W.serving_problem(*kind, seed=0)
-    p = W.Problem("serving", c.geom, c.t, c.b, c.rho.astype(np.float64))
-    g = p.geom
+@pytest.mark.parametrize("grid,aspect,fam", [(0, 0, (3, 11)), (1, 1, (0,)), (3, 2, (1, 4, 8, 15)), (2, 0, (6, 7, 17))])
+def test_serving_requests_sampled(dds, grid, aspect, fam):
+    # requests of the serving mix: grid, cell aspect dz/dx, a subset of the 18 families,
+    # evaluated as the server does -- one context of all 18 families per geometry
+    a = W.ServingArrival(0.0, grid, aspect, fam, seed=11)
+    c = W.serving_problem(a)
+    g = c.geom
+    ctx = dds.StressContext(0)
+    ctx.set_geometry(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.mu, g.nu).set_families(c.t, c.b).build_kernels()
+    got = ctx.stress_subset(list(fam), torch.from_numpy(np.ascontiguousarray(c.rho)).cuda()).cpu().numpy()
+    ctx.close()
+    got = got.reshape(6, -1)
     tg = np.unique(np.concatenate([sample_targets(g, 24, seed=7), x_line(g, g.ny // 2, 0)[::4]]))
-    got = gpu_stress(dds, p).reshape(6, -1)
-    ref = oracle.stress_direct(g, p.t, p.b, p.rho, targets=tg, use_table=False).T
+    ref = oracle.stress_direct(g, c.t[list(fam)], c.b[list(fam)], c.rho.astype(np.float64), targets=tg,
+                               use_table=False).T
     assert rel_l2_per_component(got[:, tg], ref).max() <= TOL_STRESS
 
 

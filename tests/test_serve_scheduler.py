@@ -3,7 +3,9 @@ device backend whose launches finish when the test says so.  Checked: batching o
 same-geometry requests up to max_batch, results routed to the right futures in
 order, busy contexts skipped while other contexts run, least-recently-used eviction
 under the HBM budget (never of the context about to run), requests that can never
-fit failed with MemoryError, and build failures failing only their own requests."""
+fit failed with MemoryError (a context's footprint counted before it is built), build
+failures failing only their own requests, family subsets batched only with the same
+subset, and the latency breakdown."""
 import threading
 import time
 
@@ -33,6 +35,9 @@ class FakeBackend:
         self.lock = threading.Lock()
         self.builds, self.closes, self.launches = [], [], []
         self.jobs = []
+
+    def footprint(self, req):
+        return CTX_BYTES
 
     def build(self, req):
         if self.fail_grid is not None and tuple(req.grid) == self.fail_grid:
@@ -64,6 +69,10 @@ class FakeBackend:
     @staticmethod
     def results(job):
         return job["out"]
+
+    @staticmethod
+    def timings(job):
+        return 0.5, 2.0, 1.0
 
     @staticmethod
     def pin(rho):
@@ -163,10 +172,30 @@ def test_least_recently_used_context_is_evicted():
     assert sorted(be.closes) == sorted([A, C, B, D])   # close() releases the rest
 
 
-def test_context_about_to_run_is_never_evicted():
-    # room for the buffers but not for the context too: the only idle context is the one
-    # just built, and it must not be closed under the launch (the fake asserts that)
+def test_context_footprint_is_counted_before_building():
+    # room for the buffers but not for the context too: nothing is built, the request fails
     be = FakeBackend()
+    g = (4, 2, 1)
+    budget = CTX_BYTES + io(g) - 1
+    with StressServer(hbm_budget=budget, backend=be) as srv:
+        with pytest.raises(MemoryError):
+            srv.submit(request(g, 1.0)).result(timeout=5)
+        assert be.launches == [] and be.builds == []
+        assert srv.resident == 0 and not srv.cache
+    assert be.closes == []
+    with StressServer(hbm_budget=CTX_BYTES - 1, backend=be) as srv:   # warm: the context alone
+        with pytest.raises(MemoryError):
+            srv.warm(request(g, 0.0))
+    assert be.builds == []
+
+
+def test_context_about_to_run_is_never_evicted():
+    # a backend that learns a context's size only by building it: room for the buffers
+    # but not for the context too; the only idle context is the one just built, and it
+    # must not be closed under the launch (the fake asserts that)
+    class LateSize(FakeBackend):
+        footprint = None
+    be = LateSize()
     g = (4, 2, 1)
     budget = CTX_BYTES + io(g) - 1
     with StressServer(hbm_budget=budget, backend=be) as srv:
@@ -175,6 +204,31 @@ def test_context_about_to_run_is_never_evicted():
         assert be.launches == []
         assert srv.resident == 0 and not srv.cache
     assert be.closes == [g]
+
+
+def test_family_subsets_batch_only_with_the_same_subset():
+    be = FakeBackend(n_streams=1, auto=False)
+    g = (4, 2, 1)
+    t = np.tile([[1.0, 0.0, 0.0]], (4, 1))
+
+    def sub(fam, value):
+        nx, ny, nz = g
+        return StressRequest(g, (1e-6, 1e-6, 1e-6), 1e10, 0.3, t, t.copy(),
+                             np.full((len(fam), nz, ny, nx), value, np.float32), fam=tuple(fam))
+    with StressServer(hbm_budget=1e9, max_batch=4, backend=be) as srv:
+        first = srv.submit(sub([0], 1.0))
+        wait_until(lambda: len(be.launches) == 1)
+        futs = [srv.submit(sub(f, 1.0)) for f in ([1, 2], [0], [1, 2], [3], [0])]
+        time.sleep(0.02)
+        be.auto = True
+        be.release()
+        for f, fam in zip(futs, ([1, 2], [0], [1, 2], [3], [0])):
+            expect(f, 8.0 * len(fam))
+        expect(first, 8.0)
+        br = srv.breakdown_ms()
+    assert be.builds == [g]                        # one context serves every subset
+    assert sorted(n for _, n, _ in be.launches[1:]) == [1, 2, 2]
+    assert br["device"]["p50"] == 2.0 and br["h2d"]["p99"] == 0.5 and br["queue"]["p50"] >= 0.0
 
 
 def test_requests_that_fit_only_alone_are_split():

@@ -71,3 +71,20 @@ def test_scaled_polycrystal_scales_one_pattern():
     # every column carries exactly one orientation, uniform in height
     assert np.all((a.rho > 0).sum(axis=0) == 1)
     assert np.all(a.rho[:, 0] == a.rho[:, -1])
+
+
+def test_serving_stream_draws_family_subsets_and_seeds():
+    a = W.serving_stream(0, 20.0, 200.0)
+    assert abs(len(a) / 20.0 - 200.0) < 15                      # Poisson rate
+    assert all(x.time < y.time for x, y in zip(a, a[1:]))
+    assert [x.seed for x in a] == list(range(len(a)))            # one grain seed per request
+    for x in a:
+        assert 1 <= len(x.fam) <= 4 and list(x.fam) == sorted(set(x.fam)) and all(0 <= f < 18 for f in x.fam)
+    counts = np.bincount([len(x.fam) for x in a], minlength=5)[1:]
+    assert counts.min() > 0.8 * len(a) / 4                       # family counts uniform over 1..4
+    per_family = np.bincount([f for x in a for f in x.fam], minlength=18)
+    assert per_family.min() > 0.7 * per_family.mean()            # every family drawn
+    assert W.serving_stream(0, 20.0, 200.0)[5] == a[5]           # seeded
+    s = W.serving_slots(0, 1, 3)
+    assert s.shape == (4, 64, 64, 64) and s.dtype == np.float32
+    assert np.allclose(s.sum(axis=0), W.gan_height_profile(W.serving_geometry(0, 1))[:, None, None])

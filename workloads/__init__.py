@@ -324,54 +324,80 @@ def sweep_realisation(r: int) -> Problem:
     return gan_polycrystal(g, D, r, name=f"sweep_{r}")
 
 
-# Serving stream: grids, cell aspects dz/dx (dx = dy = 0.2 um) and family sets drawn
-# per request; one Voronoi polycrystal (2 um grains) per (grid, family set) serves
-# as the density of every request of that kind.
+# Serving stream: per request a grid, a cell aspect dz/dx (dx = dy = 0.2 um), 1 to 4
+# families drawn from the 18 of gan_families(), and a grain seed (the request id).
 SERVING_GRIDS = [(64, 64, 64), (128, 128, 64), (256, 256, 128), (512, 512, 64)]
 SERVING_ASPECTS = [0.1, 0.25, 1.0]
-SERVING_FAMILY_SETS = [[0], [1, 4, 8, 15]]        # indices into gan_families(): 1 and 4 families
+SERVING_MAX_FAMILIES = 4
+
+
+@dataclass
+class ServingArrival:
+    time: float              # s after the start of the stream
+    grid: int                # index into SERVING_GRIDS
+    aspect: int              # index into SERVING_ASPECTS
+    fam: tuple               # 1..4 distinct indices into gan_families(), ascending
+    seed: int                # grain seed of the request's polycrystal
 
 
 def serving_stream(seed: int, duration: float, rate: float):
-    """Poisson arrivals at `rate` per second for `duration` seconds: list of
-    (arrival time s, grid index, aspect index, family-set index)."""
+    """Poisson arrivals at `rate` per second for `duration` seconds, as a list of
+    ServingArrival; request i draws its grid, aspect and family count uniformly, its
+    families as a uniform random subset of the 18, and grain seed i."""
     out = []
     t = 0.0
     i = 0
     while True:
-        u = uniform01(seed, np.arange(4 * i, 4 * i + 4))
+        u = uniform01(seed, np.arange(24 * i, 24 * i + 24))
         t += -math.log(1.0 - u[0]) / rate
         if t >= duration:
             return out
-        out.append((t, min(int(4 * u[1]), 3), min(int(3 * u[2]), 2), min(int(len(SERVING_FAMILY_SETS) * u[3]),
-                                                                           len(SERVING_FAMILY_SETS) - 1)))
+        k = 1 + min(int(SERVING_MAX_FAMILIES * u[3]), SERVING_MAX_FAMILIES - 1)
+        order = np.argsort(u[4:22], kind="stable")         # a uniform random permutation of 18
+        fam = tuple(sorted(int(f) for f in order[:k]))
+        out.append(ServingArrival(t, min(int(4 * u[1]), 3), min(int(3 * u[2]), 2), fam, i))
         i += 1
 
 
 @dataclass
 class ServingCase:
     geom: Geometry
-    t: np.ndarray
+    t: np.ndarray            # (18, 3): every request of the geometry shares one context
     b: np.ndarray
-    rho: np.ndarray          # (F, nz, ny, nx) float32
+    rho: np.ndarray          # (n, nz, ny, nx) float32 for the families fam
+    fam: tuple
 
 
-def serving_problem(grid_idx: int, aspect_idx: int, famset_idx: int, seed: int = 0) -> ServingCase:
-    """Density of one request kind: Voronoi columns (2 um grains) whose grains take the
-    families of the set in turn, each carrying the polycrystal height profile."""
+def serving_geometry(grid_idx: int, aspect_idx: int) -> Geometry:
     nx, ny, nz = SERVING_GRIDS[grid_idx]
     dx = 0.2 * UM
-    g = Geometry(nx, ny, nz, dx, dx, dx * SERVING_ASPECTS[aspect_idx])
+    return Geometry(nx, ny, nz, dx, dx, dx * SERVING_ASPECTS[aspect_idx])
+
+
+def serving_slots(grid_idx: int, aspect_idx: int, grain_seed: int) -> np.ndarray:
+    """The densities of up to four families of one request's polycrystal: Voronoi
+    columns (2 um grains, seeds from grain_seed) whose grains take the four family slots
+    in turn, each slot carrying the GaN height profile.  Shape (4, nz, ny, nx), float32;
+    a request with k families uses the first k slots."""
+    g = serving_geometry(grid_idx, aspect_idx)
     n_seeds = max(1, int(round(g.nx * g.dx * g.ny * g.dy / (math.pi * UM ** 2))))
-    grains = voronoi_columns(g, n_seeds, seed)
-    t18, b18 = gan_families()
-    fams = SERVING_FAMILY_SETS[famset_idx]
+    grains = voronoi_columns(g, n_seeds, grain_seed)
     prof = gan_height_profile(g).astype(np.float32)
-    rho = np.empty((len(fams), nz, ny, nx), dtype=np.float32)
-    for q in range(len(fams)):
-        mask = ((grains % len(fams)) == q).astype(np.float32)
+    rho = np.empty((SERVING_MAX_FAMILIES, g.nz, g.ny, g.nx), dtype=np.float32)
+    for q in range(SERVING_MAX_FAMILIES):
+        mask = ((grains % SERVING_MAX_FAMILIES) == q).astype(np.float32)
         np.multiply(prof[:, None, None], mask[None], out=rho[q])
-    return ServingCase(g, t18[fams].copy(), b18[fams].copy(), rho)
+    return rho
+
+
+def serving_problem(a: ServingArrival, slots: np.ndarray | None = None) -> ServingCase:
+    """The request of arrival `a` (slots: serving_slots of its geometry and grain seed,
+    when already made)."""
+    g = serving_geometry(a.grid, a.aspect)
+    if slots is None:
+        slots = serving_slots(a.grid, a.aspect, a.seed)
+    t18, b18 = gan_families()
+    return ServingCase(g, t18, b18, slots[: len(a.fam)], a.fam)
 
 
 def random_problem(geom: Geometry, t: np.ndarray, b: np.ndarray, seed: int,

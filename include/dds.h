@@ -222,10 +222,20 @@ int dds_stress_noalloc(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigm
 int dds_stress_subset(dds_ctx *ctx, int nb, int n, const int *fam, const void *rho, int rho_dtype, float *sigma,
                       void *cuda_stream);
 
-/* End-to-end variant with HOST buffers: copies rho_host (float32, [F][nz][ny][nx])
- * to the device, evaluates, copies sigma back to sigma_host (float32,
- * [6][nz][ny][nx]) and synchronises the stream.  Device staging buffers are owned
- * by the context. */
+/* End-to-end variants with HOST buffers (Eq. 10 evaluated as dds_stress, with the
+ * densities coming from and the stresses going to host memory).
+ *
+ * dds_stress_host_async: enqueues the copy of rho_host (float32, [F][nz][ny][nx]) to
+ * the device, the evaluation on `cuda_stream`, and the copy of the result to sigma_host
+ * (float32, [6][nz][ny][nx]); returns without waiting.  The copies run on two streams
+ * of the context and consecutive calls use two staging sets in turn, so one call's
+ * copies overlap the previous or next call's evaluation.  rho_host may be reused and
+ * sigma_host read only after dds_stress_host_sync; use pinned host memory for the
+ * copies to overlap.  Device staging buffers (two sets) are owned by the context.
+ * dds_stress_host_sync: waits for every call enqueued so far.
+ * dds_stress_host: one call and its sync. */
+int dds_stress_host_async(dds_ctx *ctx, const float *rho_host, float *sigma_host, void *cuda_stream);
+int dds_stress_host_sync(dds_ctx *ctx);
 int dds_stress_host(dds_ctx *ctx, const float *rho_host, float *sigma_host, void *cuda_stream);
 
 /* FP64 interaction coefficients of one family (t, b) under the current geometry

@@ -35,7 +35,7 @@ DDS_OPT_PBC_SHELLS = 4
 EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option", "dds_autotune",
            "dds_build_kernels", "dds_stress", "dds_stress_multi", "dds_stress_stats", "dds_stress_batched",
            "dds_stress_noalloc", "dds_stress_subset",
-           "dds_stress_host",
+           "dds_stress_host", "dds_stress_host_async", "dds_stress_host_sync",
            "dds_table_at", "dds_query", "dds_footprint", "dds_spectra_bytes", "dds_contract_spectra", "dds_launches_per_stress", "dds_profile_enable",
            "dds_profile_read", "dds_relax", "dds_graph_capture", "dds_graph_launch", "dds_graph_nodes",
            "dds_graph_destroy", "dds_device_status", "dds_last_error", "dds_destroy")
@@ -76,6 +76,8 @@ def load_library():
         "dds_stress_multi": ([vp, ctypes.c_int, vp, ctypes.c_int, vp, vp], ctypes.c_int),
         "dds_stress_stats": ([vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
         "dds_stress_host": ([vp, vp, vp, vp], ctypes.c_int),
+        "dds_stress_host_async": ([vp, vp, vp, vp], ctypes.c_int),
+        "dds_stress_host_sync": ([vp], ctypes.c_int),
         "dds_table_at": ([vp, dp, dp, lp, ip, dp], ctypes.c_int),
         "dds_query": ([vp, ip, ip, ip, ip], ctypes.c_int),
         "dds_spectra_bytes": ([vp, ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
@@ -205,6 +207,18 @@ def dds_stress_host(ctx, rho_host: np.ndarray, sigma_host: np.ndarray, stream=No
     _check(ctx, load_library().dds_stress_host(ctx, ctypes.c_void_p(rho_host.ctypes.data),
                                                ctypes.c_void_p(sigma_host.ctypes.data),
                                                _stream_handle(stream)))
+
+
+def dds_stress_host_async(ctx, rho_host: np.ndarray, sigma_host: np.ndarray, stream=None):
+    assert rho_host.dtype == np.float32 and rho_host.flags.c_contiguous
+    assert sigma_host.dtype == np.float32 and sigma_host.flags.c_contiguous
+    _check(ctx, load_library().dds_stress_host_async(ctx, ctypes.c_void_p(rho_host.ctypes.data),
+                                                     ctypes.c_void_p(sigma_host.ctypes.data),
+                                                     _stream_handle(stream)))
+
+
+def dds_stress_host_sync(ctx):
+    _check(ctx, load_library().dds_stress_host_sync(ctx))
 
 
 def dds_table_at(ctx, t, b, ijk) -> np.ndarray:
@@ -472,6 +486,14 @@ class StressContext:
             sigma_host = np.empty((6,) + self.shape, dtype=np.float32)
         dds_stress_host(self.handle, rho_host, sigma_host, stream)
         return sigma_host
+
+    def stress_host_async(self, rho_host: np.ndarray, sigma_host: np.ndarray, stream=None):
+        """Enqueue one host-buffer evaluation (C-contiguous float32 arrays that stay alive
+        until stress_host_sync); copies overlap the neighbouring calls' evaluations."""
+        dds_stress_host_async(self.handle, rho_host, sigma_host, stream)
+
+    def stress_host_sync(self):
+        dds_stress_host_sync(self.handle)
 
     def relax(self, sigma_dis, n_steps: int, u=None, total: bool = True, stream=None):
         """Free-surface relaxation (Sec. 5) of sigma_dis (CUDA float32, (6, nz, ny, nx)).

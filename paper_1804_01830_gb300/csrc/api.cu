@@ -861,7 +861,7 @@ void dds_graph_destroy(dds_graph *g) {
   delete g;
 }
 
-int dds_stress_host(dds_ctx *ctx, const float *rho_host, float *sigma_host, void *cuda_stream) {
+int dds_stress_host_async(dds_ctx *ctx, const float *rho_host, float *sigma_host, void *cuda_stream) {
   if (!ctx) return DDS_ERR_INVALID_ARG;
   if (!ctx->built) return fail(ctx, DDS_ERR_NOT_READY, "stress_host: call dds_build_kernels first");
   if (!rho_host || !sigma_host) return fail(ctx, DDS_ERR_INVALID_ARG, "stress_host: NULL pointer");
@@ -869,35 +869,75 @@ int dds_stress_host(dds_ctx *ctx, const float *rho_host, float *sigma_host, void
   if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "cannot make device %d current", ctx->device);
   const size_t N = (size_t)ctx->nx * ctx->ny * ctx->nz;
   const size_t rb = sizeof(float) * N * ctx->F, sb = sizeof(float) * N * 6;
-  if (ctx->h2d_rho_bytes < rb) {
-    cudaFree(ctx->h2d_rho);
-    ctx->h2d_rho = nullptr;
-    ctx->h2d_rho_bytes = 0;
-    if (cudaMalloc(&ctx->h2d_rho, rb) != cudaSuccess) {
+  cudaError_t err = cudaSuccess;
+  if (!ctx->s_in) {
+    err = cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking);
+    for (int j = 0; j < 2 && err == cudaSuccess; ++j) {
+      err = cudaEventCreateWithFlags(&ctx->ev_in[j], cudaEventDisableTiming);
+      if (err == cudaSuccess) err = cudaEventCreateWithFlags(&ctx->ev_comp[j], cudaEventDisableTiming);
+      if (err == cudaSuccess) err = cudaEventCreateWithFlags(&ctx->ev_out[j], cudaEventDisableTiming);
+    }
+    if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress_host: %s", cudaGetErrorString(err));
+  }
+  if (ctx->h2d_rho_bytes < rb || ctx->h2d_sigma_bytes < sb) {
+    // earlier calls may still use the old buffers
+    err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress_host: %s", cudaGetErrorString(err));
+    for (int j = 0; j < 2; ++j) {
+      cudaFree(ctx->h2d_rho[j]);
+      cudaFree(ctx->h2d_sigma[j]);
+      ctx->h2d_rho[j] = nullptr;
+      ctx->h2d_sigma[j] = nullptr;
+    }
+    ctx->h2d_rho_bytes = ctx->h2d_sigma_bytes = 0;
+    for (int j = 0; j < 2 && err == cudaSuccess; ++j) {
+      err = cudaMalloc(&ctx->h2d_rho[j], rb);
+      if (err == cudaSuccess) err = cudaMalloc(&ctx->h2d_sigma[j], sb);
+    }
+    if (err != cudaSuccess) {
       cudaGetLastError();
-      return fail(ctx, DDS_ERR_OOM, "stress_host: cannot allocate %zu bytes", rb);
+      return fail(ctx, DDS_ERR_OOM, "stress_host: cannot allocate 2 x %zu bytes of staging", rb + sb);
     }
     ctx->h2d_rho_bytes = rb;
-  }
-  if (ctx->h2d_sigma_bytes < sb) {
-    cudaFree(ctx->h2d_sigma);
-    ctx->h2d_sigma = nullptr;
-    ctx->h2d_sigma_bytes = 0;
-    if (cudaMalloc(&ctx->h2d_sigma, sb) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ctx, DDS_ERR_OOM, "stress_host: cannot allocate %zu bytes", sb);
-    }
     ctx->h2d_sigma_bytes = sb;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  cudaError_t err = cudaMemcpyAsync(ctx->h2d_rho, rho_host, rb, cudaMemcpyHostToDevice, s);
+  const int j = (int)(ctx->host_calls & 1);
+  // staging set j: its densities are free once the call two back has evaluated, its
+  // stresses once that call's results reached the host (waits on unrecorded events pass)
+  err = cudaStreamWaitEvent(ctx->s_in, ctx->ev_comp[j], 0);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(ctx->h2d_rho[j], rho_host, rb, cudaMemcpyHostToDevice, ctx->s_in);
+  if (err == cudaSuccess) err = cudaEventRecord(ctx->ev_in[j], ctx->s_in);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ctx->ev_in[j], 0);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(s, ctx->ev_out[j], 0);
   if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress_host: H2D copy: %s", cudaGetErrorString(err));
-  int rc = dds_stress(ctx, ctx->h2d_rho, DDS_F32, ctx->h2d_sigma, cuda_stream);
+  const int rc = dds_stress(ctx, ctx->h2d_rho[j], DDS_F32, ctx->h2d_sigma[j], cuda_stream);
   if (rc != DDS_OK) return rc;
-  err = cudaMemcpyAsync(sigma_host, ctx->h2d_sigma, sb, cudaMemcpyDeviceToHost, s);
-  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-  if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress_host: %s", cudaGetErrorString(err));
+  err = cudaEventRecord(ctx->ev_comp[j], s);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(ctx->s_out, ctx->ev_comp[j], 0);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(sigma_host, ctx->h2d_sigma[j], sb, cudaMemcpyDeviceToHost, ctx->s_out);
+  if (err == cudaSuccess) err = cudaEventRecord(ctx->ev_out[j], ctx->s_out);
+  if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress_host: D2H copy: %s", cudaGetErrorString(err));
+  ctx->host_calls++;
   return DDS_OK;
+}
+
+int dds_stress_host_sync(dds_ctx *ctx) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!ctx->s_out) return DDS_OK;
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return fail(ctx, DDS_ERR_CUDA, "cannot make device %d current", ctx->device);
+  cudaError_t err = cudaStreamSynchronize(ctx->s_in);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->s_out);
+  if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress_host_sync: %s", cudaGetErrorString(err));
+  return DDS_OK;
+}
+
+int dds_stress_host(dds_ctx *ctx, const float *rho_host, float *sigma_host, void *cuda_stream) {
+  const int rc = dds_stress_host_async(ctx, rho_host, sigma_host, cuda_stream);
+  return rc != DDS_OK ? rc : dds_stress_host_sync(ctx);
 }
 
 int dds_table_at(dds_ctx *ctx, const double t[3], const double b[3], long n, const int *ijk_host,
@@ -1012,8 +1052,15 @@ void dds_destroy(dds_ctx *ctx) {
     DeviceGuard guard(ctx->device);   // frees proceed even if it failed: they need no current device
     free_buffers(ctx);
     free_twiddles(&ctx->tw);
-    cudaFree(ctx->h2d_rho);
-    cudaFree(ctx->h2d_sigma);
+    for (int j = 0; j < 2; ++j) {
+      cudaFree(ctx->h2d_rho[j]);
+      cudaFree(ctx->h2d_sigma[j]);
+      if (ctx->ev_in[j]) cudaEventDestroy(ctx->ev_in[j]);
+      if (ctx->ev_comp[j]) cudaEventDestroy(ctx->ev_comp[j]);
+      if (ctx->ev_out[j]) cudaEventDestroy(ctx->ev_out[j]);
+    }
+    if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
+    if (ctx->s_out) cudaStreamDestroy(ctx->s_out);
     cudaFree(ctx->stats);
     cudaFree(ctx->relax_buf);
     for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);

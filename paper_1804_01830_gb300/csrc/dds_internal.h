@@ -122,9 +122,14 @@ struct dds_ctx {
   float *relax_buf = nullptr;           // relaxation: dt f, u ping-pong, surface terms
   size_t relax_n = 0;
   int stats_cap = 0;
-  void *h2d_rho = nullptr;              // staging for dds_stress_host
-  float *h2d_sigma = nullptr;
+  // staging for the host-buffer entry points: two sets, used by consecutive calls in
+  // turn so that one call's copies overlap another call's evaluation
+  void *h2d_rho[2] = {nullptr, nullptr};
+  float *h2d_sigma[2] = {nullptr, nullptr};
   size_t h2d_rho_bytes = 0, h2d_sigma_bytes = 0;
+  cudaStream_t s_in = nullptr, s_out = nullptr;     // copy streams (non-blocking)
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+  long host_calls = 0;
   // per-pass profiling
   bool profiling = false;
   std::vector<cudaEvent_t> prof_events;   // 6 per recorded evaluation

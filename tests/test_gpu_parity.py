@@ -259,6 +259,26 @@ def test_host_entry_point_matches_device_entry_point(dds):
     ctx.close()
 
 
+def test_pipelined_host_calls_match_device_calls(dds):
+    # five calls in flight through the two staging sets, each with its own densities and
+    # result buffer: every result equals the device-buffer evaluation of its densities
+    p = W.random_problem(W.Geometry(96, 80, 40, 0.2e-6, 0.2e-6, 0.05e-6),
+                         *[a[[0, 1, 9, 12]] for a in W.gan_families()], seed=8)
+    ctx = dds.context_for(p)
+    base = p.rho.astype(np.float32)
+    rhos = [np.ascontiguousarray(base * (1.0 + 0.25 * k) if k % 2 == 0 else base[:, :, :, ::-1] * (1.0 + 0.1 * k))
+            for k in range(5)]
+    rhos = [torch.from_numpy(r).pin_memory().numpy() for r in rhos]
+    outs = [torch.empty((6,) + p.geom.shape, dtype=torch.float32).pin_memory().numpy() for _ in rhos]
+    for r, o in zip(rhos, outs):
+        ctx.stress_host_async(r, o)
+    ctx.stress_host_sync()
+    for r, o in zip(rhos, outs):
+        dev = ctx.stress(torch.from_numpy(r).cuda()).cpu().numpy()
+        assert np.array_equal(dev, o)
+    ctx.close()
+
+
 def test_batched_matches_single_calls(dds):
     probs = [W.gaussian_disk_32(), W.random_problem(W.Geometry(20, 12, 6, 0.5e-6, 0.5e-6, 0.2e-6),
                                                     *[a[[2, 3, 14]] for a in W.gan_families()], seed=3)]

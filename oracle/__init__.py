@@ -23,7 +23,7 @@ _lib = None
 class OrcGeom(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("h", ctypes.c_double * 3), ("mu", ctypes.c_double), ("nu", ctypes.c_double),
-                ("n_near", ctypes.c_double), ("n_shells", ctypes.c_int)]
+                ("n_near", ctypes.c_double), ("n_shells", ctypes.c_int), ("periodic", ctypes.c_int)]
 
 
 def build(force: bool = False) -> Path:
@@ -59,6 +59,7 @@ def _load():
         lib.orc_interaction.argtypes = [gp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp]
         lib.orc_gtable.argtypes = [gp, dp, dp, dp]
         lib.orc_interaction_pbc.argtypes = [gp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        lib.orc_interaction_periodic.argtypes = [gp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp]
         lib.orc_stress_direct.argtypes = [gp, ctypes.c_int, dp, dp, dp, ctypes.c_long, lp,
                                           ctypes.c_int, dp]
         lib.orc_num_threads.restype = ctypes.c_int
@@ -74,13 +75,14 @@ def _vec(v) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(3))
 
 
-def geom_struct(geom, n_near: float = 3.0, n_shells: int = 0) -> OrcGeom:
+def geom_struct(geom, n_near: float = 3.0, n_shells: int = 0, periodic: bool = False) -> OrcGeom:
     g = OrcGeom()
     g.nx, g.ny, g.nz = int(geom.nx), int(geom.ny), int(geom.nz)
     g.h[0], g.h[1], g.h[2] = float(geom.dx), float(geom.dy), float(geom.dz)
     g.mu, g.nu = float(geom.mu), float(geom.nu)
     g.n_near = float(n_near)
     g.n_shells = int(n_shells)
+    g.periodic = int(bool(periodic))
     return g
 
 
@@ -130,17 +132,27 @@ def interaction_pbc(geom, i: int, j: int, k: int, t, b, n_shells: int, n_near: f
     return out
 
 
-def gtable(geom, t, b, n_near: float = 3.0, n_shells: int = 0) -> np.ndarray:
+def interaction_periodic(geom, i: int, j: int, k: int, t, b, n_shells: int, n_near: float = 3.0) -> np.ndarray:
+    """Periodic reading of the replica sum: images of the minimal in-plane offset (i, j)
+    mod (nx, ny) within n_shells periods, ties at half a period averaged; one family."""
+    lib = _load()
+    g = geom_struct(geom, n_near, n_shells, periodic=True)
+    out = np.zeros(6)
+    lib.orc_interaction_periodic(ctypes.byref(g), int(i), int(j), int(k), _dp(_vec(t)), _dp(_vec(b)), _dp(out))
+    return out
+
+
+def gtable(geom, t, b, n_near: float = 3.0, n_shells: int = 0, periodic: bool = False) -> np.ndarray:
     """Full table, shape (2nz-1, 2ny-1, 2nx-1, 6); index [k+nz-1, j+ny-1, i+nx-1]."""
     lib = _load()
-    g = geom_struct(geom, n_near, n_shells)
+    g = geom_struct(geom, n_near, n_shells, periodic)
     out = np.zeros((2 * geom.nz - 1, 2 * geom.ny - 1, 2 * geom.nx - 1, 6))
     lib.orc_gtable(ctypes.byref(g), _dp(_vec(t)), _dp(_vec(b)), _dp(out))
     return out
 
 
 def stress_direct(geom, t, b, rho, targets=None, n_near: float = 3.0,
-                  use_table: bool | None = None, n_shells: int = 0) -> np.ndarray:
+                  use_table: bool | None = None, n_shells: int = 0, periodic: bool = False) -> np.ndarray:
     """Eq. 10 summed over families by direct summation.
 
     rho: (F, nz, ny, nx) in m^-2; targets: linear cell indices (default: all cells).
@@ -157,7 +169,7 @@ def stress_direct(geom, t, b, rho, targets=None, n_near: float = 3.0,
     if use_table is None:
         n_off = (2 * geom.nx - 1) * (2 * geom.ny - 1) * (2 * geom.nz - 1)
         use_table = n_off * 48 <= 256 * 2 ** 20 and n_off <= 4 * targets.size * geom.n_cells
-    g = geom_struct(geom, n_near, n_shells)
+    g = geom_struct(geom, n_near, n_shells, periodic)
     out = np.zeros((targets.size, 6))
     lib.orc_stress_direct(ctypes.byref(g), F, _dp(t), _dp(b), _dp(rho), targets.size,
                           targets.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), int(bool(use_table)),

@@ -271,9 +271,44 @@ void orc_interaction_pbc(const orc_geom *g, int i, int j, int k, const double t[
   for (int c = 0; c < 6; ++c) out[c] = acc[c];
 }
 
+/* Images of the offset along one axis of period n: the minimal image r in (-n/2, n/2]
+ * and, at the tie r = n/2 (n even), also -n/2 with weight 1/2 each. */
+static int minimal_images(int i, int n, int r[2], double w[2]) {
+  int m = i % n;
+  if (m < 0) m += n;
+  if (2 * m < n) {
+    r[0] = m;
+  } else if (2 * m > n) {
+    r[0] = m - n;
+  } else {
+    r[0] = m;
+    r[1] = -m;
+    w[0] = w[1] = 0.5;
+    return 2;
+  }
+  w[0] = 1.0;
+  return 1;
+}
+
+void orc_interaction_periodic(const orc_geom *g, int i, int j, int k, const double t[3], const double b[3],
+                              double out[6]) {
+  int rx[2], ry[2];
+  double wx[2], wy[2];
+  const int nxr = minimal_images(i, g->nx, rx, wx), nyr = minimal_images(j, g->ny, ry, wy);
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int a = 0; a < nxr; ++a)
+    for (int c2 = 0; c2 < nyr; ++c2) {
+      double s[6];
+      orc_interaction_pbc(g, rx[a], ry[c2], k, t, b, s);
+      for (int c = 0; c < 6; ++c) acc[c] += wx[a] * wy[c2] * s[c];
+    }
+  for (int c = 0; c < 6; ++c) out[c] = acc[c];
+}
+
 static void coefficient(const orc_geom *g, int i, int j, int k, const double t[3], const double b[3],
                         double out[6]) {
-  if (g->n_shells > 0) orc_interaction_pbc(g, i, j, k, t, b, out);
+  if (g->n_shells > 0 && g->periodic) orc_interaction_periodic(g, i, j, k, t, b, out);
+  else if (g->n_shells > 0) orc_interaction_pbc(g, i, j, k, t, b, out);
   else orc_interaction(g, i, j, k, t, b, out);
 }
 

@@ -24,6 +24,9 @@ typedef struct {
   double n_near;   /* near field: |offset| < n_near * max(h) is subdivided (Sec. 2.3) */
   int n_shells;    /* in-plane periodic boundary conditions with replica shells |k|,|l| <= n_shells
                       (Sec. 4, Eq. 12-13); 0: open boundary */
+  int periodic;    /* with n_shells > 0: 1 = the replica shells are centred on each source's
+                      minimal image (periodic reading, see orc_interaction_periodic); 0 = on
+                      the in-system offset (orc_interaction_pbc) */
 } orc_geom;
 
 /* Eq. 4a-4c with Eq. 5: stress of a segment parallel to z from (0,0,zA) to
@@ -60,6 +63,16 @@ void orc_interaction_pbc(const orc_geom *g, int i, int j, int k, const double t[
 /* Full table over offsets i in [-(nx-1), nx-1] (same for j, k), layout
  * out[((k + nz-1) * (2ny-1) + (j + ny-1)) * (2nx-1) + (i + nx-1)][6]. */
 void orc_gtable(const orc_geom *g, const double t[3], const double b[3], double *out);
+
+/* Periodic reading of Sec. 4's replica sum: for the in-plane offset (i, j) taken modulo
+ * (nx, ny), the images of the source column nearest to the target -- the minimal image
+ * i* in (-nx/2, nx/2] shifted by m nx, |m| <= n_shells, and likewise in y -- summed;
+ * where the offset is exactly half a period (nx even, i* = nx/2) the two image sets
+ * starting at +nx/2 and -nx/2 are averaged, so the coefficients stay odd.  Exactly
+ * periodic in i and j; the same n_shells -> infinity limit as orc_interaction_pbc.
+ * out[6]. */
+void orc_interaction_periodic(const orc_geom *g, int i, int j, int k, const double t[3], const double b[3],
+                              double out[6]);
 
 /* Eq. 10 summed over families (Eq. 12 with n_shells > 0): sigma at the listed target cells (linear index
  * (k*ny + j)*nx + i) by direct summation over all source cells.

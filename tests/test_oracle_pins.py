@@ -385,6 +385,57 @@ def test_replica_table_is_odd():
     assert rel(tab[::-1, ::-1, ::-1], -tab) < 1e-13
 
 
+# ---------------------------------------------- periodic reading (Sec. 4) --
+def test_periodic_reading_is_a_cyclic_convolution():
+    """The periodic reading (replica shells centred on each source's minimal image) makes
+    sigma exactly covariant under cyclic shifts of rho in x and y; the in-system-offset
+    reading is not (the test has teeth)."""
+    g = W.Geometry(8, 6, 3, 1e-6, 1e-6, 0.25e-6, MU, NU)
+    t18, b18 = W.gan_families()
+    p = W.random_problem(g, t18[[0, 9]], b18[[0, 9]], seed=4)
+    shifted = np.roll(p.rho, (2, 3), axis=(2, 3))
+    for periodic, tol in ((True, 1e-12), (False, None)):
+        s0 = oracle.stress_direct(g, p.t, p.b, p.rho, n_shells=3, periodic=periodic).T.reshape(6, 3, 6, 8)
+        s1 = oracle.stress_direct(g, p.t, p.b, shifted, n_shells=3, periodic=periodic).T.reshape(6, 3, 6, 8)
+        err = rel(s1, np.roll(s0, (2, 3), axis=(2, 3)))
+        if tol is not None:
+            assert err < tol
+        else:
+            assert err > 1e-4
+
+
+def test_periodic_table_is_odd_and_periodic():
+    g = W.Geometry(8, 6, 4, 1e-6, 1e-6, 0.25e-6, MU, NU)
+    tab = oracle.gtable(g, W.t_mixed(), (BB, 0.3 * BB, 1.6 * BB), n_shells=3, periodic=True)
+    assert rel(tab[::-1, ::-1, ::-1], -tab) < 1e-13
+    # offset i and i - nx are the same column of sources (index i + nx - 1 vs i - 1)
+    assert rel(tab[:, :, g.nx:], tab[:, :, : g.nx - 1]) < 1e-15
+    assert rel(tab[:, g.ny:, :], tab[:, : g.ny - 1, :]) < 1e-15
+    # a half-period offset is the mean of its two minimal images
+    t, b = (0, 0, 1), (BB, 0, 0)
+    half = oracle.interaction_periodic(g, 4, 1, 2, t, b, 3)
+    two = 0.5 * (oracle.interaction_pbc(g, 4, 1, 2, t, b, 3) + oracle.interaction_pbc(g, -4, 1, 2, t, b, 3))
+    assert rel(half, two) < 1e-15
+
+
+def test_periodic_reading_converges_as_the_paper_states_and_meets_the_other():
+    gold = _read_golden("pbc_sec4.txt")
+    acc = float(gold["accuracy"])
+    g = W.Geometry(16, 16, 8, 1e-6, 1e-6, 1e-6, MU, NU)
+    rng = np.random.default_rng(1)
+    offs = list(zip(rng.integers(0, 16, 30), rng.integers(0, 16, 30), rng.integers(-7, 8, 30)))
+    for t, b in [([0, 0, 1], [BB, 0, 0]), ([0, 0, 1], [0, 0, BB]), (W.t_mixed(), [BB, 0, 1.6 * BB])]:
+        ref = np.array([oracle.interaction_periodic(g, *o, t, b, 80) for o in offs])
+        scale = np.abs(ref).max(axis=0)
+        for n in (int(gold["shells_low"]), int(gold["shells_high"])):
+            F = np.array([oracle.interaction_periodic(g, *o, t, b, n) for o in offs])
+            E = np.array([oracle.interaction_pbc(g, *o, t, b, n) for o in offs])   # the other reading
+            for c in range(6):
+                if scale[c] > 1e-12 * scale.max():
+                    assert np.abs(F[:, c] - ref[:, c]).max() < acc * scale[c], (t, b, n, c)
+                    assert np.abs(E[:, c] - ref[:, c]).max() < 2 * acc * scale[c], (t, b, n, c)
+
+
 # ------------------------------------------------------- mirror parities --
 PAIRS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))   # xx, yy, zz, xy, xz, yz
 

@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-relax", action="store_true", help="skip the free-surface relaxation measurement")
     ap.add_argument("--no-grain", action="store_true", help="skip the grain-size scaling study")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 64-realisation batched sweep")
+    ap.add_argument("--no-pbc", action="store_true", help="skip the periodic-boundary comparison")
     return ap.parse_args()
 
 
@@ -390,6 +391,44 @@ def grain_scaling_study(device: int):
               for i, c in ((0, "xx"), (1, "yy"), (3, "xy"), (2, "zz"))}
         out[name] = {"grid": [n, n, nz], "thickness_um": H / um, "grain_sizes_um": [D / um for D in Ds],
                      "exponents": ex, "predicted": want}
+    return out
+
+
+def pbc_benchmark(device: int, shells: int = 2, steps: int = 10):
+    """The GaN layer (256x256x128, 18 families) with in-plane periodic boundary conditions
+    (Sec. 4): the in-system-offset reading on the zero-padded FFT against the periodic
+    reading, whose FFT is unpadded in y.  ms per evaluation (L2 flushed before each),
+    per pass, and the pass-model bytes."""
+    import torch
+    import paper_1804_01830_gb300 as dds
+    p = W.CONFIGS["gan_layer_256x256x128"]()
+    g = p.geom
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho, dtype=np.float32)).cuda(device)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=rho.device)
+    out = {"workload": "gan_layer_256x256x128", "replica_shells": shells}
+    for name, periodic in (("zero_padded", 0), ("periodic_in_y", 1)):
+        ctx = dds.StressContext(device)
+        ctx.set_geometry(g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.mu, g.nu).set_families(p.t, p.b)
+        ctx.set_option(dds.DDS_OPT_PBC_SHELLS, shells).set_option(dds.DDS_OPT_PBC_PERIODIC, periodic)
+        t0 = time.perf_counter()
+        ctx.build_kernels()
+        build_s = time.perf_counter() - t0
+        sig = torch.empty((6,) + g.shape, dtype=torch.float32, device=rho.device)
+        for _ in range(3):
+            ctx.stress(rho, sig)
+        dds.dds_profile_enable(ctx.handle, True)
+        for _ in range(steps):
+            flush.zero_()
+            ctx.stress(rho, sig)
+        pp = dds.dds_profile_read(ctx.handle, steps).mean(axis=0)
+        q = ctx.query()
+        pb = pass_bytes(p, q)
+        out[name] = {"padded": [q["px"], q["py"], q["pz"]], "ms_per_step": float(pp.sum()),
+                     "cells_per_s": g.n_cells / (float(pp.sum()) * 1e-3),
+                     "passes_ms": {n: float(v) for n, v in zip(PASS_NAMES, pp)},
+                     "bytes_pass_model": int(sum(pb.values())), "kernel_build_s": build_s}
+        ctx.close()
+    out["bytes_ratio_periodic_over_padded"] = out["periodic_in_y"]["bytes_pass_model"] / out["zero_padded"]["bytes_pass_model"]
     return out
 
 
@@ -824,6 +863,10 @@ def run_ours(args):
     if not args.no_grain and rank == 0 and world == 1:
         grain = grain_scaling_study(local)
 
+    pbc = None
+    if not args.no_pbc and rank == 0 and world == 1:
+        pbc = pbc_benchmark(local)
+
     sweep = None
     if not args.no_sweep and rank == 0 and world == 1:
         sweep = sweep_benchmark(local)
@@ -879,6 +922,7 @@ def run_ours(args):
         "serving": serving,
         "relaxation": relaxation,
         "grain_size_scaling": grain,
+        "periodic_boundary": pbc,
         "batched_sweep": sweep,
         "cpu_baseline": cpu,
         "cpu_fft_baseline": cpu_fft,

@@ -75,6 +75,15 @@ enum {
                               the paper finds 15-20 shells accurate to 3%); the table
                               build costs (2n + 1)^2 times more.  0 (default): open
                               boundary.  Invalidates built kernels. */
+  DDS_OPT_PBC_PERIODIC = 5,/* with DDS_OPT_PBC_SHELLS = n > 0: 1 centres the replica shells
+                              of Sec. 4 on each source's minimal image (the in-plane offset
+                              taken modulo the period; at exactly half a period the two
+                              image sets averaged), so sigma is a cyclic convolution in x and
+                              y; the FFT is then unpadded in y (ny must be a power of two
+                              >= 32), which halves the y and z passes' work.  0 (default):
+                              shells centred on the in-system offset, zero-padded FFT.  Both
+                              readings share the n -> infinity limit.  Invalidates built
+                              kernels. */
   DDS_OPT_SPECTRA_FP16 = 3,/* 1: store the cached kernel spectra as FP16 with one FP32
                               scale per (component, field) -- half the bytes of the
                               dominant pass; arithmetic stays FP32.  Error: about 1e-4

@@ -30,6 +30,7 @@ DDS_OPT_NEAR_RADIUS = 1
 DDS_OPT_Z_LANES = 2
 DDS_OPT_SPECTRA_FP16 = 3
 DDS_OPT_PBC_SHELLS = 4
+DDS_OPT_PBC_PERIODIC = 5
 
 # Every symbol include/dds.h declares.
 EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option", "dds_autotune",

@@ -157,19 +157,46 @@ __device__ void coef_cell(const CoefGeom &g, int i, int j, int k, V3 t, V3 b, do
 
 // With periodic boundary conditions (Sec. 4, Eq. 13): the sum over the replicas of the
 // source cell, r_i + (k Lx, l Ly, 0), |k|, |l| <= n_shells.
+// Replica sum of Eq. 13 around in-plane offset (i, j): images (i + kk nx, j + ll ny).
+__device__ void coef_replicas(const CoefGeom &g, int i, int j, int k, V3 t, V3 b, double w, double acc[6]) {
+  for (int kk = -g.n_shells; kk <= g.n_shells; ++kk)
+    for (int ll = -g.n_shells; ll <= g.n_shells; ++ll) {
+      double s[6];
+      coef_cell(g, i + kk * g.nx, j + ll * g.ny, k, t, b, s);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[c] += w * s[c];
+    }
+}
+
+// Minimal image of offset i for period n, in (-n/2, n/2]; at the tie n/2 (n even) also
+// -n/2, each with weight 1/2.  Returns the number of images (1 or 2).
+__device__ __forceinline__ int min_images(int i, int n, int r[2], double w[2]) {
+  int m = i % n;
+  if (m < 0) m += n;
+  w[0] = 1.0;
+  if (2 * m < n) { r[0] = m; return 1; }
+  if (2 * m > n) { r[0] = m - n; return 1; }
+  r[0] = m;
+  r[1] = -m;
+  w[0] = w[1] = 0.5;
+  return 2;
+}
+
 __device__ void coef_any(const CoefGeom &g, int i, int j, int k, V3 t, V3 b, double out[6]) {
   if (g.n_shells <= 0) {
     coef_cell(g, i, j, k, t, b, out);
     return;
   }
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int kk = -g.n_shells; kk <= g.n_shells; ++kk)
-    for (int ll = -g.n_shells; ll <= g.n_shells; ++ll) {
-      double s[6];
-      coef_cell(g, i + kk * g.nx, j + ll * g.ny, k, t, b, s);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) acc[c] += s[c];
-    }
+  if (!g.periodic) {
+    coef_replicas(g, i, j, k, t, b, 1.0, acc);
+  } else {             // shells centred on the minimal image, ties averaged (odd, periodic)
+    int rx[2], ry[2];
+    double wx[2], wy[2];
+    const int nxr = min_images(i, g.nx, rx, wx), nyr = min_images(j, g.ny, ry, wy);
+    for (int a = 0; a < nxr; ++a)
+      for (int c2 = 0; c2 < nyr; ++c2) coef_replicas(g, rx[a], ry[c2], k, t, b, wx[a] * wy[c2], acc);
+  }
 #pragma unroll
   for (int c = 0; c < 6; ++c) out[c] = acc[c];
 }
@@ -463,6 +490,7 @@ CoefGeom coef_geom(const dds_ctx *ctx) {
   g.nx = ctx->nx;
   g.ny = ctx->ny;
   g.n_shells = ctx->n_shells;
+  g.periodic = ctx->pbc_periodic ? 1 : 0;
   return g;
 }
 

@@ -75,6 +75,7 @@ struct CoefGeom {
   double rn2;         // squared near-field radius (n_near * max h)^2
   int nx, ny;         // grid (replica periods)
   int n_shells;       // > 0: replica shells of the in-plane periodic boundary conditions
+  int periodic;       // with n_shells > 0: shells centred on each source's minimal image
 };
 
 // Twiddle tables exp(-2 pi i k / P) for P = 16 .. 2048 (see dds_fft.cuh).
@@ -94,6 +95,7 @@ struct dds_ctx {
   double mu = 0, nu = 0;
   double n_near = 3.0;
   int n_shells = 0;                     // in-plane periodic boundary conditions (Sec. 4); 0: open
+  bool pbc_periodic = false;            // periodic reading of the replica sum, FFT periodic in y
   int z_lanes = 0;                      // fused z pass: 0 auto, -1 shared-memory kernel, G lanes/column
   int z_wz = 0;                         // shared-memory z tile width chosen by dds_autotune (0: planner)
   bool tuned = false;                   // z_lanes / z_wz were set by dds_autotune

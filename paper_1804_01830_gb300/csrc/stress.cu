@@ -194,6 +194,16 @@ cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in
                      const float2 *tw, cudaStream_t s) {
   constexpr int W = YTile<PY>::W, T = YTile<PY>::NT;
   const long tiles = (long)nf * sh.nz * (sh.M / W) + (long)nf * ((sh.nz + W - 1) / W);
+  if (sh.py == sh.ny) {                   // periodic in y: no zero padding (py <= 512)
+    if constexpr (PY <= 512) {
+      const size_t smem = sizeof(float2) * yr::y_smem<PY, W>();
+      cudaError_t err = prep(yr::k_ypass_st<PY, W, T, INV, true>, smem);
+      if (err != cudaSuccess) return err;
+      yr::k_ypass_st<PY, W, T, INV, true><<<(unsigned)tiles, T, smem, s>>>(sh, nf, im, in, om, on, tw);
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+  }
   if constexpr (INV && PY >= 1024) {
     // 1024-row inverse: the shared-memory Stockham tile with 16-byte row stores (radial
     // disk 512x512x16: 0.137 ms, against 0.152 for the register stages on 4-column

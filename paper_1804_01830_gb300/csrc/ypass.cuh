@@ -10,9 +10,10 @@
 //   rows k1 + R1 k2 straight to global memory.
 // Threads are numbered with the column fastest, so the shared-memory accesses of a
 // warp are contiguous and its global stores are runs of W complex values per row.
-// The forward input is zero from row ny on and ny <= P/2, so stage 1 reads only
-// n1 < R1/2 and splits the R1-point DFT into two R1/2-point DFTs; the inverse keeps
-// rows k < ny <= P/2, so stage 2 computes only k2 < R2/2.
+// With zero padding (FULL false) the forward input is zero from row ny on and
+// ny <= P/2, so stage 1 reads only n1 < R1/2 and splits the R1-point DFT into two
+// R1/2-point DFTs; the inverse keeps rows k < ny <= P/2, so stage 2 computes only
+// k2 < R2/2.  FULL (periodic in y, P = ny): every row is read and kept.
 #pragma once
 #include "stress_common.cuh"
 
@@ -32,7 +33,7 @@ template <int P, int W> __host__ __device__ constexpr int y_smem() {
   return P * W > YCfg<P>::R1 * y_stride<P, W>() ? P * W : YCfg<P>::R1 * y_stride<P, W>();
 }
 
-template <int PY, int W, int NT, bool INV>
+template <int PY, int W, int NT, bool INV, bool FULL = false>
 __global__ void __launch_bounds__(NT) k_ypass_st(Shape sh, int nf, const float2 *__restrict__ in_main,
                                                  const float2 *__restrict__ in_nyq, float2 *__restrict__ out_main,
                                                  float2 *__restrict__ out_nyq, const float2 *__restrict__ tw) {
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(NT) k_ypass_st(Shape sh, int nf, const float2 
 
   // stage 1: items (n2, w), column fastest; all reads before the barrier, then writes
   constexpr int I1 = (W * R2 + NT - 1) / NT;
-  constexpr int N1 = INV ? R1 : R1 / 2;       // non-zero inputs per column
+  constexpr int N1 = (INV || FULL) ? R1 : R1 / 2;   // non-zero inputs per column
   float2 v[I1][N1];
 #pragma unroll
   for (int it = 0; it < I1; ++it) {
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(NT) k_ypass_st(Shape sh, int nf, const float2 
     if ((W * R2) % NT != 0 && item >= W * R2) continue;
     const int n2 = item / W, w = item - n2 * W;
     float2 x[R1];
-    if constexpr (!INV) {
+    if constexpr (!INV && !FULL) {
       constexpr int H = R1 / 2;
       float2 ev[H], od[H];
 #pragma unroll
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(NT) k_ypass_st(Shape sh, int nf, const float2 
     } else {
 #pragma unroll
       for (int n1 = 0; n1 < R1; ++n1) x[n1] = v[it][n1];
-      dft_reg<R1, true>(x);
+      dft_reg<R1, INV>(x);
     }
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(NT) k_ypass_st(Shape sh, int nf, const float2 
 
   // stage 2: items (k1, w)
   constexpr int I2 = (W * R1 + NT - 1) / NT;
-  constexpr int K2 = INV ? R2 / 2 : R2;
+  constexpr int K2 = (INV && !FULL) ? R2 / 2 : R2;
 #pragma unroll
   for (int it = 0; it < I2; ++it) {
     const int item = tid + it * NT;

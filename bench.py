@@ -190,11 +190,11 @@ def measured_peaks():
 # Sources that define each pass's kernels: a committed ncu traffic record stays valid
 # while these files are unchanged.
 KERNEL_SOURCES = {
-    "z_fused": ("zpass_impl.cuh", "zpass_f32.cu", "dds_fft.cuh", "stress_common.cuh"),
-    "x_fwd": ("xpass.cuh", "dds_fft.cuh", "stress_common.cuh"),
-    "x_inv": ("xpass.cuh", "bulk.cuh", "dds_fft.cuh", "stress_common.cuh"),
-    "y_fwd": ("ypass.cuh", "dds_fft.cuh", "stress_common.cuh"),
-    "y_inv": ("stress.cu", "ypass.cuh", "dds_fft.cuh", "stress_common.cuh"),
+    "z_fused": ("zpass_impl.cuh", "zfour.cuh", "zpass_f32.cu", "dds_fft.cuh", "stress_common.cuh", "dds_internal.h"),
+    "x_fwd": ("xpass.cuh", "dds_fft.cuh", "stress_common.cuh", "dds_internal.h"),
+    "x_inv": ("xpass.cuh", "bulk.cuh", "dds_fft.cuh", "stress_common.cuh", "dds_internal.h"),
+    "y_fwd": ("ypass.cuh", "dds_fft.cuh", "stress_common.cuh", "dds_internal.h"),
+    "y_inv": ("stress.cu", "ypass.cuh", "dds_fft.cuh", "stress_common.cuh", "dds_internal.h"),
 }
 
 
@@ -795,10 +795,26 @@ def run_ours(args):
         for _ in range(3):
             ctx.stress_host(rh, sh)
         dt_sync = (time.perf_counter() - t1) / 3
+        # the host link as this run sees it: plain copies of the same buffers
+        rd = torch.empty_like(rho_h, device="cuda")
+        sd = torch.empty_like(sig_h, device="cuda")
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        for _ in range(3):
+            rd.copy_(rho_h, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_gbs = 3 * rho_h.numel() * 4 / (time.perf_counter() - t2) / 1e9
+        t2 = time.perf_counter()
+        for _ in range(3):
+            sig_h.copy_(sd, non_blocking=True)
+        torch.cuda.synchronize()
+        d2h_gbs = 3 * sig_h.numel() * 4 / (time.perf_counter() - t2) / 1e9
+        del rd, sd
         e2e = {"value": whole_job_rate(world, g.n_cells * ke, dt), "unit": UNIT,
                "h2d_bytes_per_step": int(rho_h.numel() * 4), "d2h_bytes_per_step": int(sig_h.numel() * 4),
                "steps": ke, "ms_per_step": 1e3 * dt / ke,
                "ms_per_step_one_at_a_time": 1e3 * dt_sync,
+               "host_link_gbs": {"h2d": h2d_gbs, "d2h": d2h_gbs},
                "api": "dds_stress_host_async per step, dds_stress_host_sync at the end"}
 
     # reduced storage: the same workload with FP16 kernel spectra

@@ -143,9 +143,9 @@ __global__ void __launch_bounds__(ZF<PZ>::NT, 512 / ZF<PZ>::NT)
 
   // stage 1: forward R1-point DFTs over n1 of the rows n2 + 8 n1 (n1 < R1/2 non-zero);
   // a negated-frequency tile transforms -s_b conj(rho) (s_b folds the spectra's sign)
-  for (int item = tid; item < FE * R2 * W; item += NT) {
+  constexpr int NI = FE * R2 * W;              // items (field, n2, column)
+  auto s1_load = [&](int item, float2 (&ev)[H]) {
     const int e = item / (R2 * W), r = item - e * (R2 * W), n2 = r / W, w = r - n2 * W;
-    float2 ev[H], od[H];
 #pragma unroll
     for (int n1 = 0; n1 < H; ++n1) {
       const int z = n2 + R2 * n1;
@@ -154,11 +154,15 @@ __global__ void __launch_bounds__(ZF<PZ>::NT, 512 / ZF<PZ>::NT)
         ev[n1] = !nyq ? __ldg(in_main + (((long)e * nz + z) * py + ky) * M + kxt * W + w)
                       : __ldg(in_nyq + ((long)e * py + nyq_idx * W + w) * nz + z);
     }
-    if (sw) {                                 // after all loads are issued
+  };
+  auto s1_finish = [&](int item, float2 (&ev)[H]) {
+    const int e = item / (R2 * W), r = item - e * (R2 * W), n2 = r / W, w = r - n2 * W;
+    if (sw) {
       const float sy = ((sh.zs.sbneg >> e) & 1u) ? -1.0f : 1.0f;
 #pragma unroll
       for (int n1 = 0; n1 < H; ++n1) ev[n1] = make_float2(-sy * ev[n1].x, sy * ev[n1].y);
     }
+    float2 od[H];
 #pragma unroll
     for (int n1 = 0; n1 < H; ++n1) od[n1] = rot_const<false>(ev[n1], n1, R1);
     dft_reg<H, false>(ev);                    // outputs k1 = 2 j
@@ -169,6 +173,16 @@ __global__ void __launch_bounds__(ZF<PZ>::NT, 512 / ZF<PZ>::NT)
       T[(2 * j) * SK] = j == 0 ? ev[0] : cmul_tw<false>(ev[j], twP[n2 * 2 * j]);
       T[(2 * j + 1) * SK] = cmul_tw<false>(od[j], twP[n2 * (2 * j + 1)]);
     }
+  };
+  // items in pairs of rounds: both items' rows are requested before either is transformed
+  // (five fields give 1.25 items per thread; GaN layer 1.11 -> 1.07 ms)
+  for (int item = tid; item < NI; item += 2 * NT) {
+    float2 a[H], b[H];
+    const bool two = item + NT < NI;
+    s1_load(item, a);
+    if (two) s1_load(item + NT, b);
+    s1_finish(item, a);
+    if (two) s1_finish(item + NT, b);
   }
   __syncthreads();
 

@@ -597,8 +597,10 @@ def serving_benchmark(device: int, duration: float, rate: float = 200.0, budget:
     for a in first.values():                       # build every geometry's context, 4-family buffers
         srv.warm(request(W.ServingArrival(0.0, a.grid, a.aspect, (0, 1, 2, 3), 0)))
     build_s = time.perf_counter() - t0
-    for a in first.values():                       # untimed: one request per geometry primes the buffers
-        srv.submit(request(a)).result(timeout=600)
+    for a in first.values():                       # untimed: as many requests per geometry as
+        futs = [srv.submit(request(a)) for _ in range(n_streams)]   # streams prime the pinned
+        for f in futs:                                               # result buffers
+            f.result(timeout=600)
     srv.latencies.clear()
     srv.records.clear()
 

@@ -207,20 +207,22 @@ __global__ void __launch_bounds__(ZF<PZ>::NT, 512 / ZF<PZ>::NT)
     float2 s[R2];
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) s[k2] = make_float2(0.f, 0.f);
+    // this component's other fields load now, before the prefetched ones are used
+    ZRaw<GT, (FE > PF ? FE - PF : 1)> lt;
+    if constexpr (FE > PF) lt.load(kc, PF, tid, NT);
 #pragma unroll
-    for (int e = 0; e < FE; ++e) {
+    for (int e = 0; e < PF; ++e) {
       const float sc = kscale != nullptr ? __ldg(kscale + c * FE + e) : 1.0f;
-      if (e < PF) {
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) s[k2] = cmadd_i(s[k2], gr.get(e, k2, sc), f[e][k2]);
-      } else {
-        ZRaw<GT, 1> late;
-        late.load(kc, e, tid, NT);
-#pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) s[k2] = cmadd_i(s[k2], late.get(0, k2, sc), f[e][k2]);
-      }
+      for (int k2 = 0; k2 < R2; ++k2) s[k2] = cmadd_i(s[k2], gr.get(e, k2, sc), f[e][k2]);
     }
     if (c < 5) gr.load(kc + (long)FE * PZ * W, 0, tid, NT);
+#pragma unroll
+    for (int e = PF; e < FE; ++e) {
+      const float sc = kscale != nullptr ? __ldg(kscale + c * FE + e) : 1.0f;
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) s[k2] = cmadd_i(s[k2], lt.get(e - PF, k2, sc), f[e][k2]);
+    }
     dft_reg<R2, true>(s);                     // index a of n = a + 8 b
     float2 *Y = zsm + (long)c * R2 * SY + k1 * W + w;
     Y[0] = s[0];

@@ -165,12 +165,15 @@ def pass_bytes(p, q):
     c8 = 8
     x_spec = m1 * ny * nz * c8          # one field after the x pass
     y_spec = m1 * py * nz * c8          # one field after the y pass (rows z < nz)
+    if q.get("yx_cluster"):             # fused inverse y + x: the x-inverse interval holds it
+        inv = {"y_inv": 0, "x_inv": 6 * y_spec + 6 * N * 4}
+    else:
+        inv = {"y_inv": 6 * y_spec + 6 * x_spec, "x_inv": 6 * x_spec + 6 * N * 4}
     return {
         "x_fwd": fin * N * 4 + fe * x_spec,
         "y_fwd": fe * x_spec + fe * y_spec,
         "z_fused": fe * y_spec + spectra_bytes(q) + 6 * y_spec,
-        "y_inv": 6 * y_spec + 6 * x_spec,
-        "x_inv": 6 * x_spec + 6 * N * 4,
+        **inv,
     }
 
 
@@ -192,7 +195,8 @@ def measured_peaks():
 KERNEL_SOURCES = {
     "z_fused": ("zpass_impl.cuh", "zfour.cuh", "zpass_f32.cu", "dds_fft.cuh", "stress_common.cuh", "dds_internal.h"),
     "x_fwd": ("xpass.cuh", "dds_fft.cuh", "stress_common.cuh", "dds_internal.h"),
-    "x_inv": ("xpass.cuh", "bulk.cuh", "dds_fft.cuh", "stress_common.cuh", "dds_internal.h"),
+    "x_inv": ("xpass.cuh", "bulk.cuh", "yxpass.cuh", "ypass.cuh", "stress.cu", "dds_fft.cuh", "stress_common.cuh",
+              "dds_internal.h"),
     "y_fwd": ("ypass.cuh", "dds_fft.cuh", "stress_common.cuh", "dds_internal.h"),
     "y_inv": ("stress.cu", "ypass.cuh", "dds_fft.cuh", "stress_common.cuh", "dds_internal.h"),
 }

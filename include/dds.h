@@ -84,6 +84,16 @@ enum {
                               shells centred on the in-system offset, zero-padded FFT.  Both
                               readings share the n -> infinity limit.  Invalidates built
                               kernels. */
+  DDS_OPT_YX_FUSED = 6,    /* 1: run the inverse y and x transforms as one pass, one
+                              thread-block cluster per output plane (c, z) exchanging the
+                              plane through distributed shared memory, where the plane
+                              fits (zero-padded y, padded sizes py x px/2 of 256 x 128,
+                              512 x 128, 256 x 256 or 512 x 256) and the device can hold
+                              the cluster; elsewhere two separate passes.  It moves 44%
+                              fewer bytes but is slower on GB300 (GaN layer 256x256x128:
+                              0.51 ms against 0.37 for the two passes).  0 (default):
+                              separate passes.  Same result up to rounding.  Invalidates
+                              built kernels. */
   DDS_OPT_SPECTRA_FP16 = 3,/* 1: store the cached kernel spectra as FP16 with one FP32
                               scale per (component, field) -- half the bytes of the
                               dominant pass; arithmetic stays FP32.  Error: about 1e-4
@@ -286,10 +296,17 @@ int dds_contract_spectra(const void *rho_hat, int fe, const float *g, void *sigm
 /* Number of kernel launches one dds_stress call issues. */
 int dds_launches_per_stress(const dds_ctx *ctx);
 
+/* CTAs per cluster of the fused inverse y + x pass that a built context runs (see
+ * DDS_OPT_YX_FUSED), or 0 when it runs the two inverse passes separately.  Negative:
+ * INVALID_ARG (NULL) or NOT_READY (not built). */
+int dds_yx_cluster(const dds_ctx *ctx);
+
 /* Per-pass timing.  While enabled, every dds_stress on this context records CUDA
  * events on its stream before the first pass and after each pass (the passes are
- * x forward, y forward, fused z, y inverse, x inverse).  Timing only; results are
- * unchanged.  Enabling clears earlier records. */
+ * x forward, y forward, fused z, y inverse, x inverse; with the fused inverse pass
+ * of DDS_OPT_YX_FUSED the y-inverse interval is empty and the x-inverse interval
+ * holds the fused pass).  Timing only; results are unchanged.  Enabling clears
+ * earlier records. */
 int dds_profile_enable(dds_ctx *ctx, int enable);
 
 /* Synchronise the recorded events and return their durations: ms_out (host,

@@ -31,13 +31,15 @@ DDS_OPT_Z_LANES = 2
 DDS_OPT_SPECTRA_FP16 = 3
 DDS_OPT_PBC_SHELLS = 4
 DDS_OPT_PBC_PERIODIC = 5
+DDS_OPT_YX_FUSED = 6
 
 # Every symbol include/dds.h declares.
 EXPORTS = ("dds_create", "dds_set_geometry", "dds_set_families", "dds_set_option", "dds_autotune",
            "dds_build_kernels", "dds_stress", "dds_stress_multi", "dds_stress_stats", "dds_stress_batched",
            "dds_stress_noalloc", "dds_stress_subset",
            "dds_stress_host", "dds_stress_host_async", "dds_stress_host_sync",
-           "dds_table_at", "dds_query", "dds_footprint", "dds_spectra_bytes", "dds_contract_spectra", "dds_launches_per_stress", "dds_profile_enable",
+           "dds_table_at", "dds_query", "dds_footprint", "dds_spectra_bytes", "dds_contract_spectra", "dds_launches_per_stress", "dds_yx_cluster",
+           "dds_profile_enable",
            "dds_profile_read", "dds_relax", "dds_graph_capture", "dds_graph_launch", "dds_graph_nodes",
            "dds_graph_destroy", "dds_device_status", "dds_last_error", "dds_destroy")
 
@@ -85,6 +87,7 @@ def load_library():
         "dds_footprint": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
         "dds_contract_spectra": ([vp, ctypes.c_int, vp, vp, ctypes.c_longlong, vp], ctypes.c_int),
         "dds_launches_per_stress": ([vp], ctypes.c_int),
+        "dds_yx_cluster": ([vp], ctypes.c_int),
         "dds_profile_enable": ([vp, ctypes.c_int], ctypes.c_int),
         "dds_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ip, ip], ctypes.c_int),
         "dds_relax": ([vp, vp, vp, ctypes.c_int, vp, vp], ctypes.c_int),
@@ -236,7 +239,7 @@ def dds_query(ctx):
     v = [ctypes.c_int() for _ in range(4)]
     _check(ctx, load_library().dds_query(ctx, *[ctypes.byref(x) for x in v]))
     return {"n_fields": v[0].value, "px": v[1].value, "py": v[2].value, "pz": v[3].value,
-            "spectra_bytes": dds_spectra_bytes(ctx)}
+            "spectra_bytes": dds_spectra_bytes(ctx), "yx_cluster": dds_yx_cluster(ctx)}
 
 
 def dds_footprint(ctx, nb: int = 1) -> int:
@@ -259,6 +262,13 @@ def dds_contract_spectra(rho_hat_ptr: int, fe: int, g_ptr: int, sigma_hat_ptr: i
 
 def dds_launches_per_stress(ctx) -> int:
     return int(load_library().dds_launches_per_stress(ctx))
+
+
+def dds_yx_cluster(ctx) -> int:
+    """CTAs per cluster of the fused inverse y + x pass (0: two separate passes)."""
+    v = int(load_library().dds_yx_cluster(ctx))
+    _check(ctx, min(v, 0))
+    return v
 
 
 def dds_profile_enable(ctx, enable: bool = True):

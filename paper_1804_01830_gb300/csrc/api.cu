@@ -248,6 +248,7 @@ int make_plan(dds_ctx *ctx) {
   sh.zreg_g = 0;
   sh.zfour = 0;
   sh.nb = 1;
+  sh.yxf = ctx->yx_fused ? yx_inv_cluster(sh) : 0;
   if (sh.pz <= 64 && sh.fe <= 4 && ctx->z_lanes >= 0) {
     // register-only z pass: E = pz / G registers per lane, E in {8, 16}
     int G = ctx->z_lanes;
@@ -495,6 +496,12 @@ int dds_set_option(dds_ctx *ctx, int key, double value) {
       if (value != 0.0 && value != 1.0)
         return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: periodic reading must be 0 or 1");
       ctx->pbc_periodic = value != 0.0;
+      invalidate(ctx);
+      return DDS_OK;
+    case DDS_OPT_YX_FUSED:
+      if (value != 0.0 && value != 1.0)
+        return fail(ctx, DDS_ERR_INVALID_ARG, "set_option: fused inverse pass must be 0 or 1");
+      ctx->yx_fused = value != 0.0;
       invalidate(ctx);
       return DDS_OK;
     case DDS_OPT_NEAR_RADIUS:
@@ -1041,6 +1048,12 @@ int dds_spectra_bytes(const dds_ctx *ctx, unsigned long long *bytes) {
 int dds_launches_per_stress(const dds_ctx *ctx) {
   if (!ctx || !ctx->built) return 0;
   return ctx->fe == 0 ? 0 : stress_launch_count(ctx->shape, ctx->col);
+}
+
+int dds_yx_cluster(const dds_ctx *ctx) {
+  if (!ctx) return DDS_ERR_INVALID_ARG;
+  if (!ctx->built) return DDS_ERR_NOT_READY;
+  return ctx->shape.yxf;
 }
 
 int dds_profile_enable(dds_ctx *ctx, int enable) {

@@ -51,6 +51,7 @@ struct Shape {
   int zfour;          // 1: three-stage register z pass (pz 128 or 256, wz = zfour_width(pz))
   int nb;             // density sets evaluated together (batch); fields are [b][e], outputs [b][c]
   ZSym zs;            // zfour: stored-spectrum symmetries and layout
+  int yxf;            // > 0: fused inverse y + x pass, one cluster of yxf CTAs per plane
 };
 
 // Columns per tile of the three-stage z pass (Shape::zfour) for padded z size pz.
@@ -116,6 +117,7 @@ struct dds_ctx {
   float *kscale = nullptr;              // FP16 storage: scale per (component, field); else null
   size_t kspec_floats = 0;              // number of stored values
   bool spectra_fp16 = false;            // option: store the kernel spectra as FP16
+  bool yx_fused = false;                // option: fused inverse y + x pass where it applies
   float2 *bufA = nullptr, *bufB = nullptr;        // main work buffers
   float2 *nyqA = nullptr, *nyqB = nullptr;        // Nyquist-column buffers
   size_t bufA_n = 0, bufB_n = 0, nyqA_n = 0, nyqB_n = 0;
@@ -166,6 +168,11 @@ int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, c
                    double *stats = nullptr, float *s_out = nullptr, const Collapse *sub = nullptr,
                    int sub_fin = 0);
 int stress_launch_count(const Shape &sh, const Collapse &col);
+
+// CTAs per cluster of the fused inverse y + x pass for this shape on the current
+// device (the plane fits one cluster's shared memory and the device can hold such a
+// cluster), else 0: the plan keeps the separate y and x inverse passes.
+int yx_inv_cluster(const Shape &sh);
 
 // Free-surface relaxation (Sec. 5): n_steps explicit steps on u, then sigma_tot.
 int enqueue_relax(dds_ctx *ctx, const float *sig, float *u, int n_steps, float *sig_tot, cudaStream_t s);

@@ -27,6 +27,7 @@
 #include "stress_common.cuh"
 #include "xpass.cuh"
 #include "ypass.cuh"
+#include "yxpass.cuh"
 
 namespace dds {
 
@@ -249,6 +250,70 @@ cudaError_t launch_x_inv(const Shape &sh, const float2 *im, const float2 *in, fl
   return cudaGetLastError();
 }
 
+// Fused inverse y + x pass (yxpass.cuh): one cluster of Cfg::CL CTAs per output plane.
+template <int PY, int M>
+cudaError_t launch_yx_inv(const Shape &sh, const float2 *im, const float2 *in, float *sigma, const float2 *tw,
+                          cudaStream_t s, double *stats) {
+  using C = yx::Cfg<PY, M>;
+  auto kernel = yx::k_yx_inv<PY, M>;
+  const size_t smem = sizeof(float2) * C::SMEM_F2;
+  cudaError_t err = prep(kernel, smem);
+  if (err == cudaSuccess && C::CL > 8)
+    err = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (err != cudaSuccess) return err;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(6L * sh.nb * sh.nz * C::CL), 1, 1);
+  cfg.blockDim = dim3(C::NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C::CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  err = cudaLaunchKernelEx(&cfg, kernel, sh, im, in, sigma, tw, stats);
+  return err != cudaSuccess ? err : cudaGetLastError();
+}
+
+// How many clusters of the fused pass the device holds at once (0: none fits).
+template <int PY, int M>
+int yx_clusters_resident() {
+  using C = yx::Cfg<PY, M>;
+  auto kernel = yx::k_yx_inv<PY, M>;
+  const size_t smem = sizeof(float2) * C::SMEM_F2;
+  if (prep(kernel, smem) != cudaSuccess) return 0;
+  if (C::CL > 8 && cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C::CL, 1, 1);
+  cfg.blockDim = dim3(C::NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C::CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t dispatch_yx_inv(const Shape &sh, const float2 *im, const float2 *in, float *sigma, const float2 *tw,
+                            cudaStream_t s, double *stats) {
+  if (sh.py == 256 && sh.M == 128) return launch_yx_inv<256, 128>(sh, im, in, sigma, tw, s, stats);
+  if (sh.py == 512 && sh.M == 128) return launch_yx_inv<512, 128>(sh, im, in, sigma, tw, s, stats);
+  if (sh.py == 256 && sh.M == 256) return launch_yx_inv<256, 256>(sh, im, in, sigma, tw, s, stats);
+  if (sh.py == 512 && sh.M == 256) return launch_yx_inv<512, 256>(sh, im, in, sigma, tw, s, stats);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t dispatch_x_fwd(const Shape &sh, const Collapse &col, const void *rho, bool bf16, float2 *om,
                            float2 *on, const float2 *tw, cudaStream_t s) {
   switch (sh.M) {
@@ -292,6 +357,16 @@ cudaError_t dispatch_x_inv(const Shape &sh, const float2 *im, const float2 *in, 
 
 }  // namespace
 
+int yx_inv_cluster(const Shape &sh) {
+  if (sh.py == sh.ny || 2 * sh.ny > sh.py) return 0;       // the fused pass keeps rows y < py / 2
+  int n = 0, cl = 0;
+  if (sh.py == 256 && sh.M == 128) { n = yx_clusters_resident<256, 128>(); cl = yx::Cfg<256, 128>::CL; }
+  else if (sh.py == 512 && sh.M == 128) { n = yx_clusters_resident<512, 128>(); cl = yx::Cfg<512, 128>::CL; }
+  else if (sh.py == 256 && sh.M == 256) { n = yx_clusters_resident<256, 256>(); cl = yx::Cfg<256, 256>::CL; }
+  else if (sh.py == 512 && sh.M == 256) { n = yx_clusters_resident<512, 256>(); cl = yx::Cfg<512, 256>::CL; }
+  return n > 0 ? cl : 0;
+}
+
 int stress_launch_count(const Shape &sh, const Collapse &col) {
   int direct = 0, accum = 0;
   for (int g = 0; g < col.ngroups; ++g) {
@@ -299,7 +374,7 @@ int stress_launch_count(const Shape &sh, const Collapse &col) {
     if (col.nf[g] == 1 && col.nd[g] == 1) direct = 1;
     else accum = 1;
   }
-  return 4 + direct + accum;
+  return (sh.yxf > 0 ? 3 : 4) + direct + accum;
 }
 
 int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, cudaStream_t s, int nb,
@@ -334,10 +409,13 @@ int enqueue_stress(dds_ctx *ctx, const void *rho, int rho_dtype, float *sigma, c
   if (err == cudaSuccess)
     err = dispatch_z(sh, ctx->bufB, ctx->nyqB, ctx->kspec, ctx->kscale, ctx->bufA, ctx->nyqA, tw, s);
   mark(3);
-  if (err == cudaSuccess) err = dispatch_y<true>(sh, 6 * nb, ctx->bufA, ctx->nyqA, ctx->bufB, ctx->nyqB, tw, s);
+  if (err == cudaSuccess && sh.yxf == 0)
+    err = dispatch_y<true>(sh, 6 * nb, ctx->bufA, ctx->nyqA, ctx->bufB, ctx->nyqB, tw, s);
   mark(4);
   if (err == cudaSuccess && stats != nullptr) err = cudaMemsetAsync(stats, 0, sizeof(double) * 6 * nb * sh.nz, s);
-  if (err == cudaSuccess) err = dispatch_x_inv(sh, ctx->bufB, ctx->nyqB, sigma, tw, s, stats);
+  if (err == cudaSuccess)
+    err = sh.yxf > 0 ? dispatch_yx_inv(sh, ctx->bufA, ctx->nyqA, sigma, tw, s, stats)
+                     : dispatch_x_inv(sh, ctx->bufB, ctx->nyqB, sigma, tw, s, stats);
   if (err == cudaSuccess && stats != nullptr) {
     const long n = 6L * nb * sh.nz;
     k_stats_finish<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(stats, n, 1.0 / ((double)sh.nx * sh.ny), s_out);
@@ -356,8 +434,12 @@ int enqueue_stress_buffers(dds_ctx *ctx, const void *rho, int rho_dtype, float *
   cudaError_t err = dispatch_x_fwd(sh, ctx->col, rho, rho_dtype == DDS_BF16, bufA, nyqA, tw, s);
   if (err == cudaSuccess) err = dispatch_y<false>(sh, sh.fe, bufA, nyqA, bufB, nyqB, tw, s);
   if (err == cudaSuccess) err = dispatch_z(sh, bufB, nyqB, ctx->kspec, ctx->kscale, bufA, nyqA, tw, s);
-  if (err == cudaSuccess) err = dispatch_y<true>(sh, 6, bufA, nyqA, bufB, nyqB, tw, s);
-  if (err == cudaSuccess) err = dispatch_x_inv(sh, bufB, nyqB, sigma, tw, s);
+  if (sh.yxf > 0) {
+    if (err == cudaSuccess) err = dispatch_yx_inv(sh, bufA, nyqA, sigma, tw, s, nullptr);
+  } else {
+    if (err == cudaSuccess) err = dispatch_y<true>(sh, 6, bufA, nyqA, bufB, nyqB, tw, s);
+    if (err == cudaSuccess) err = dispatch_x_inv(sh, bufB, nyqB, sigma, tw, s);
+  }
   if (err != cudaSuccess) return fail(ctx, DDS_ERR_CUDA, "stress: kernel launch failed: %s", cudaGetErrorString(err));
   return DDS_OK;
 }

@@ -261,6 +261,14 @@ def gan_layer_128(seed: int = 0) -> Problem:
     return gan_polycrystal(g, 2.0 * UM, seed, name="gan_layer_128x128x128")
 
 
+def gan_layer_256_thin(seed: int = 0) -> Problem:
+    """The GaN layer's cells, grains, families and height profile on a 256x256x32 grid:
+    the same in-plane transforms as the 256x256x128 layer (padded 512 x 512) on a quarter
+    of its planes, for profiling captures that must stay small."""
+    g = Geometry(256, 256, 32, 0.2 * UM, 0.2 * UM, 0.05 * UM)
+    return gan_polycrystal(g, 2.0 * UM, seed, name="gan_layer_256x256x32")
+
+
 SWEEP_GRIDS = [(128, 128, 64), (128, 128, 128), (256, 256, 64), (256, 256, 128)]
 
 
@@ -416,4 +424,5 @@ CONFIGS = {
     "radial_disk_512x512x16": radial_disk_512,
     "gan_layer_256x256x128": gan_layer_256,
     "gan_layer_128x128x128": gan_layer_128,
+    "gan_layer_256x256x32": gan_layer_256_thin,
 }

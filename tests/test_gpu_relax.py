@@ -82,6 +82,8 @@ def smooth_load(shape, h, seed):
     ((4, 16, 16), (1e-6, 1e-6, 1e-6), [3, 100]),
     ((2, 7, 9), (0.2e-6, 0.2e-6, 0.05e-6), [1, 50]),       # two layers, odd sides
     ((3, 1, 32), (1e-6, 1e-6, 1e-6), [40]),                # plane strain (ny = 1)
+    ((35, 9, 66), (0.2e-6, 0.2e-6, 0.05e-6), [1, 20]),     # two x tiles of the pair kernel, two z chunks
+    ((34, 5, 67), (0.2e-6, 0.2e-6, 0.05e-6), [1, 20]),     # odd nx: one-cell kernel, two z chunks
 ])
 def test_steps_match_oracle(dds, shape, h, steps):
     sig = smooth_load(shape, h, seed=sum(shape))

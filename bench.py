@@ -778,6 +778,7 @@ def run_ours(args):
         peak, peak_src = 6800.0, "fallback"
     achieved = pb[dom_name] / (mean_pass[dom] * 1e-3) / 1e9
     step_bytes = sum(pb.values())
+    full_model = (4 * p.n_families + 144 * q["n_fields"] + 312) * p.geom.n_cells
 
     # end to end through the host-buffer entry point, pinned buffers
     e2e = None
@@ -937,7 +938,11 @@ def run_ours(args):
                      "peak_source": peak_src},
         "passes_ms": {n: float(v) for n, v in zip(PASS_NAMES, mean_pass)},
         "step_roofline": {"bytes_pass_model": step_bytes, "bytes_floor": floor_bytes(p, q),
-                          "frac_pass_model": step_bytes / (total_ms / K * 1e-3) / 1e9 / peak},
+                          "frac_pass_model": step_bytes / (total_ms / K * 1e-3) / 1e9 / peak,
+                          # the planned schedule's model with full kernel spectra,
+                          # (4 F_in + 144 F_e + 312) B per cell
+                          "bytes_full_spectra_model": full_model,
+                          "frac_full_spectra_model": full_model / (total_ms / K * 1e-3) / 1e9 / peak},
         "e2e": e2e,
         "gpu_comparator": comparator,
         "reduced_storage": reduced,

@@ -360,10 +360,18 @@ __device__ __forceinline__ float4 load_quad(const void *rho, long o) {
 
 // Groups with one family and one field (DIRECT) transform that family scaled by its
 // coefficient; the others sum coef * rho over the group's families for each field.
-// (at most 170 registers, three CTAs per SM: the 256-point summed-family kernel would
-// otherwise take 176 and fit two; GaN layer 0.239 -> 0.233 ms)
+// CTAs per SM the register budget is set for.  256 points: three, at most 170
+// registers -- the summed-family kernel would otherwise take 176 and fit two; GaN layer
+// 0.239 -> 0.233 ms.  128 points: four, 128 registers -- left free it takes 182 (two per
+// SM), and bound to three it takes 163 and runs 18% slower.  512 points: direct groups
+// four (radial disk 0.042 ms left free at 207 registers, 0.036 at three or four); summed
+// families the compiler's choice (254 registers; bound to three they spill 312 bytes).
+template <int M, bool DIRECT> constexpr int x_fwd_ctas() {
+  return M == 256 ? 3 : (M == 128 ? 4 : (M == 512 && DIRECT ? 4 : 1));
+}
+
 template <int M, bool BF16, bool DIRECT>
-__global__ void __launch_bounds__(THREADS, 3)
+__global__ void __launch_bounds__(THREADS, (x_fwd_ctas<M, DIRECT>()))
 k_x_fwd_reg(Shape sh, Collapse col, GroupList gl, const void *__restrict__ rho_v, float2 *__restrict__ out_main,
             float2 *__restrict__ out_nyq, const float2 *__restrict__ tw) {
   constexpr int R1 = FwdCfg<M>::R1, R2 = FwdCfg<M>::R2, T = R1 / 2, CPT = R2 / T, H = R1 / 2;

@@ -68,3 +68,21 @@ def test_pass_model_per_cell_closed_form():
     p = SimpleNamespace(geom=W.Geometry(nx, ny, nz, 1e-6, 1e-6, 1e-6), n_families=fin)
     per_cell = sum(bench.pass_bytes(p, q).values()) / (nx * ny * nz)
     assert abs(per_cell - (4 * fin + 144 * fe + 312)) / per_cell < 1e-3    # the Nyquist column
+
+
+def test_roofline_per_cell_figures_match_the_exact_model():
+    # the per-cell figures bench.py divides by the dominant kernel's time (the planned
+    # schedule's model, spectra read in full) are the large-grid limit of pass_bytes
+    nx, ny, nz, fin, fe = 4096, 64, 32, 18, 5
+    q = {"n_fields": fe, "px": 2 * nx, "py": 2 * ny, "pz": 2 * nz}
+    p = SimpleNamespace(geom=W.Geometry(nx, ny, nz, 1e-6, 1e-6, 1e-6), n_families=fin)
+    exact = bench.pass_bytes(p, q)
+    model = bench.pass_model_per_cell(p, q)
+    assert model == {"x_fwd": 4 * fin + 8 * fe, "y_fwd": 24 * fe, "z_fused": 112 * fe + 96, "y_inv": 144,
+                     "x_inv": 72}
+    for k in exact:
+        assert abs(exact[k] / (nx * ny * nz) - model[k]) / model[k] < 1e-3, k
+    # the GaN layer: 656 bytes per cell for the fused z pass, 5.50 GB per launch
+    g = W.Geometry(256, 256, 128, 1e-6, 1e-6, 1e-6)
+    assert bench.pass_model_per_cell(SimpleNamespace(geom=g, n_families=18), {"n_fields": 5})["z_fused"] \
+        * g.n_cells == 5_502_926_848

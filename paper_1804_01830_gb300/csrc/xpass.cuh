@@ -167,7 +167,9 @@ template <int M> struct InvTma {
   static constexpr int R1 = InvCfg<M>::R1, R2 = InvCfg<M>::R2, T = R2 / 2;
   static constexpr int LPB = THREADS / T, S = R2 * (R1 + 1) + line_pad<T>();
   static constexpr int SLOT = (LPB * M > LPB * S ? LPB * M : LPB * S);       // float2 per slot
-  static constexpr size_t SMEM = sizeof(float2) * 2 * SLOT + 2 * sizeof(uint64_t);
+  // two slots, two barriers, then the M twiddles exp(-2 pi i m / M), which stage 1 reads
+  // at scattered indices (staged once per persistent CTA)
+  static constexpr size_t SMEM = sizeof(float2) * 2 * SLOT + 2 * sizeof(uint64_t) + sizeof(float2) * M;
 };
 
 __device__ __forceinline__ long nyq_index(const Shape &sh, long line) {
@@ -186,13 +188,15 @@ k_x_inv_tma(Shape sh, const float2 *__restrict__ in_main, const float2 *__restri
   static_assert(R1 * R2 == M && RPT >= 1 && RPT * T == R1, "x inverse config");
   extern __shared__ __align__(16) float2 dsm[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(dsm + 2 * C::SLOT);
+  float2 *stwM = reinterpret_cast<float2 *>(bar + 2);
   const int t = threadIdx.x % T, lw = threadIdx.x / T;
   const bool t0 = t == 0;
   const int ca = t, cb = t0 ? R2 / 2 : R2 - t;
   const long L = 6L * sh.nb * sh.nz * sh.ny;
   const long ntiles = (L + LPB - 1) / LPB;
   const long stride = gridDim.x;
-  const float2 *twM = tw + tw_offset(M);
+  for (int i = threadIdx.x; i < M; i += THREADS) stwM[i] = __ldg(tw + tw_offset(M) + i);
+  const float2 *twM = stwM;
   const float2 *tw2 = tw + tw_offset(2 * M);
   const int nxh = (sh.nx + 1) >> 1;
   const bool even = (sh.nx & 1) == 0;
@@ -261,8 +265,8 @@ k_x_inv_tma(Shape sh, const float2 *__restrict__ in_main, const float2 *__restri
 #pragma unroll
     for (int m1 = 0; m1 < R1; ++m1) {
       if (m1 > 0) {
-        za[m1] = cmul_tw<true>(za[m1], __ldg(twM + ca * m1));
-        zb[m1] = cmul_tw<true>(zb[m1], __ldg(twM + cb * m1));
+        za[m1] = cmul_tw<true>(za[m1], twM[ca * m1]);
+        zb[m1] = cmul_tw<true>(zb[m1], twM[cb * m1]);
       }
       ls[ca * LD + m1] = za[m1];
       ls[cb * LD + m1] = zb[m1];
@@ -382,6 +386,11 @@ k_x_fwd_reg(Shape sh, Collapse col, GroupList gl, const void *__restrict__ rho_v
   constexpr int LPB = THREADS / T, S = R1 * LD + PADL;
   static_assert(R1 * R2 == M && CPT >= 1 && CPT * T == R2 && CPT <= 2, "x forward config");
   __shared__ float2 sm[LPB * S];
+  // lines of up to 256 points: the M and 2M twiddles staged in shared memory (GaN layer
+  // 0.233 -> 0.220 ms; for 512 points, eight lines per CTA, the staging costs more than
+  // it saves: radial disk 0.036 -> 0.044 ms)
+  constexpr bool STW = M <= 256;
+  __shared__ float2 stw[STW ? 3 * M : 1];
   const int t = threadIdx.x % T, lw = threadIdx.x / T;
   const long L = (long)sh.ny * sh.nz;
   const long N = L * sh.nx;
@@ -394,8 +403,12 @@ k_x_fwd_reg(Shape sh, Collapse col, GroupList gl, const void *__restrict__ rho_v
   const int nxh = (sh.nx + 1) >> 1;
   const bool even = (sh.nx & 1) == 0;
   const bool quad = (sh.nx & 3) == 0;               // rows and column pairs 16-byte aligned
-  const float2 *twM = tw + tw_offset(M);
-  const float2 *tw2 = tw + tw_offset(2 * M);
+  if constexpr (STW) {
+    for (int i = threadIdx.x; i < M; i += THREADS) stw[i] = __ldg(tw + tw_offset(M) + i);
+    for (int i = threadIdx.x; i < 2 * M; i += THREADS) stw[M + i] = __ldg(tw + tw_offset(2 * M) + i);
+  }
+  const float2 *twM = STW ? stw : tw + tw_offset(M);
+  const float2 *tw2 = STW ? stw + M : tw + tw_offset(2 * M);
   const int ra = t, rb = t0 ? R1 / 2 : R1 - t;
   float2 *ls = sm + lw * S;
 
@@ -459,6 +472,7 @@ k_x_fwd_reg(Shape sh, Collapse col, GroupList gl, const void *__restrict__ rho_v
     }
   }
   const float dscale = DIRECT ? col.coef[col.f0[g]][0] : 1.f;
+  if constexpr (STW) __syncthreads();                // twiddles staged
 
 #pragma unroll
   for (int d = 0; d < NDM; ++d) {
@@ -482,8 +496,8 @@ k_x_fwd_reg(Shape sh, Collapse col, GroupList gl, const void *__restrict__ rho_v
       for (int j = 0; j < H; ++j) {
         const int k0 = 2 * j, k1 = 2 * j + 1;
         float2 y0 = ev[j], y1 = od[j];
-        if (k0 > 0) y0 = cmul_tw<false>(y0, __ldg(twM + n2 * k0));
-        y1 = cmul_tw<false>(y1, __ldg(twM + n2 * k1));
+        if (k0 > 0) y0 = cmul_tw<false>(y0, twM[n2 * k0]);
+        y1 = cmul_tw<false>(y1, twM[n2 * k1]);
         ls[k0 * LD + n2] = y0;
         ls[k1 * LD + n2] = y1;
       }
@@ -506,8 +520,8 @@ k_x_fwd_reg(Shape sh, Collapse col, GroupList gl, const void *__restrict__ rho_v
         const float2 am = t0 ? ya[(R2 - k2) % R2] : yb[R2 - 1 - k2];
         const float2 bm = t0 ? yb[R2 - 1 - k2] : ya[R2 - 1 - k2];
         const int ka = ra + R1 * k2, kb = rb + R1 * k2;
-        __stcs(dst + ka, r2c_post(ya[k2], am, __ldg(tw2 + ka), scale));
-        __stcs(dst + kb, r2c_post(yb[k2], bm, __ldg(tw2 + kb), scale));
+        __stcs(dst + ka, r2c_post(ya[k2], am, tw2[ka], scale));
+        __stcs(dst + kb, r2c_post(yb[k2], bm, tw2[kb], scale));
       }
       if (t0) {
         const int z = (int)(line / sh.ny), y = (int)(line - (long)z * sh.ny);

@@ -197,7 +197,7 @@ cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in
   const long tiles = (long)nf * sh.nz * (sh.M / W) + (long)nf * ((sh.nz + W - 1) / W);
   if (sh.py == sh.ny) {                   // periodic in y: no zero padding (py <= 512)
     if constexpr (PY <= 512) {
-      const size_t smem = sizeof(float2) * yr::y_smem<PY, W>();
+      const size_t smem = sizeof(float2) * yr::y_smem_all<PY, W, INV, true>();
       cudaError_t err = prep(yr::k_ypass_st<PY, W, T, INV, true>, smem);
       if (err != cudaSuccess) return err;
       yr::k_ypass_st<PY, W, T, INV, true><<<(unsigned)tiles, T, smem, s>>>(sh, nf, im, in, om, on, tw);
@@ -215,7 +215,7 @@ cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in
     k_ypass<PY, W, T, INV><<<(unsigned)tiles, T, smem, s>>>(sh, nf, im, in, om, on, tw);
     return cudaGetLastError();
   }
-  const size_t smem = sizeof(float2) * yr::y_smem<PY, W>();
+  const size_t smem = sizeof(float2) * yr::y_smem_all<PY, W, INV, false>();
   cudaError_t err = prep(yr::k_ypass_st<PY, W, T, INV>, smem);
   if (err != cudaSuccess) return err;
   yr::k_ypass_st<PY, W, T, INV><<<(unsigned)tiles, T, smem, s>>>(sh, nf, im, in, om, on, tw);

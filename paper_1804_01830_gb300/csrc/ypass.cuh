@@ -33,12 +33,23 @@ template <int P, int W> __host__ __device__ constexpr int y_smem() {
   return P * W > YCfg<P>::R1 * y_stride<P, W>() ? P * W : YCfg<P>::R1 * y_stride<P, W>();
 }
 
+// Whether the tile stages the PY twiddles in shared memory (after its y_smem values):
+// stage 1 reads them at scattered indices.  Half-row forward passes up to 512 rows gain
+// (GaN layer 0.190 -> 0.176 ms); passes that read every row gain at 256 rows but lose at
+// 512 (0.215 -> 0.224 ms: one CTA per SM fewer), and 1024 rows lose in both directions.
+template <int PY, bool INV, bool FULL> __host__ __device__ constexpr bool y_stw() {
+  return PY <= 512 && ((!INV && !FULL) || PY <= 256);
+}
+template <int PY, int W, bool INV, bool FULL> __host__ __device__ constexpr int y_smem_all() {
+  return y_smem<PY, W>() + (y_stw<PY, INV, FULL>() ? PY : 0);
+}
+
 template <int PY, int W, int NT, bool INV, bool FULL = false>
 __global__ void __launch_bounds__(NT) k_ypass_st(Shape sh, int nf, const float2 *__restrict__ in_main,
                                                  const float2 *__restrict__ in_nyq, float2 *__restrict__ out_main,
                                                  float2 *__restrict__ out_nyq, const float2 *__restrict__ tw) {
   constexpr int R1 = YCfg<PY>::R1, R2 = YCfg<PY>::R2, ST = y_stride<PY, W>();
-  extern __shared__ __align__(16) float2 sm[];              // y_smem<PY, W>() values
+  extern __shared__ __align__(16) float2 sm[];              // y_smem_all<PY, W, INV, FULL>() values
   const int tid = threadIdx.x;
   const int M = sh.M, nz = sh.nz;
   const int rows_in = INV ? PY : sh.ny;
@@ -82,6 +93,10 @@ __global__ void __launch_bounds__(NT) k_ypass_st(Shape sh, int nf, const float2 
       else sm[n * W + w] = make_float2(0.f, 0.f);
     }
   }
+  constexpr bool STW = y_stw<PY, INV, FULL>();
+  float2 *stw = sm + y_smem<PY, W>();
+  if constexpr (STW)
+    for (int i = tid; i < PY; i += NT) stw[i] = __ldg(tw + tw_offset(PY) + i);
   cp_async_wait_all();
   __syncthreads();
 
@@ -100,7 +115,7 @@ __global__ void __launch_bounds__(NT) k_ypass_st(Shape sh, int nf, const float2 
     }
   }
   __syncthreads();
-  const float2 *twP = tw + tw_offset(PY);
+  const float2 *twP = STW ? stw : tw + tw_offset(PY);
 #pragma unroll
   for (int it = 0; it < I1; ++it) {
     const int item = tid + it * NT;
@@ -130,7 +145,7 @@ __global__ void __launch_bounds__(NT) k_ypass_st(Shape sh, int nf, const float2 
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       float2 y = x[k1];
-      if (k1 > 0) y = cmul_tw<INV>(y, __ldg(twP + n2 * k1));
+      if (k1 > 0) y = cmul_tw<INV>(y, STW ? twP[n2 * k1] : __ldg(twP + n2 * k1));
       sm[k1 * ST + n2 * W + w] = y;
     }
   }

@@ -145,9 +145,10 @@ int dds_build_kernels(dds_ctx *ctx, void *cuda_stream);
  * dds_set_geometry / dds_set_families and before dds_build_kernels: times one full
  * evaluation (synthetic densities and spectra; the schedule does not change the
  * arithmetic's result beyond rounding) for every fused-z-pass schedule that applies
- * -- the register kernel with each valid number of lanes per (kx, ky) column and the
- * shared-memory kernel with each valid tile width -- and keeps the fastest for the
- * build that follows.  Allocates temporary device memory and synchronises the
+ * -- the register kernel with each valid number of lanes per (kx, ky) column, the
+ * three-stage register kernel and the shared-memory kernel with each valid tile
+ * width -- on the median of five trials, each after a 256 MB write that empties L2,
+ * and keeps the fastest for the build that follows.  Allocates temporary device memory and synchronises the
  * stream.  *best_ms (host, may be NULL) receives the fastest evaluation time.
  * DDS_OPT_Z_LANES set later overrides the choice. */
 int dds_autotune(dds_ctx *ctx, void *cuda_stream, float *best_ms);

@@ -597,19 +597,20 @@ int dds_autotune(dds_ctx *ctx, void *cuda_stream, float *best_ms) {
     if (err == cudaSuccess && ctx->kscale) err = cudaMemsetAsync(ctx->kscale, 0, 6 * sizeof(float) * ctx->fe, s);
     for (int w = 0; w < 2 && rc == DDS_OK && err == cudaSuccess; ++w) rc = enqueue_stress(ctx, rho, DDS_F32, sigma, s);
     if (rc != DDS_OK || err != cudaSuccess) break;
-    float ms = 0.f;
+    // median of five trials, each from a cold L2: one disturbed trial cannot decide
+    float trial[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (int r = 0; r < 5 && rc == DDS_OK && err == cudaSuccess; ++r) {
       err = cudaMemsetAsync(flush, r, flush_bytes, s);
       if (err == cudaSuccess) err = cudaEventRecord(e0, s);
       if (err == cudaSuccess) rc = enqueue_stress(ctx, rho, DDS_F32, sigma, s);
       if (err == cudaSuccess) err = cudaEventRecord(e1, s);
       if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-      float one = 0.f;
-      if (err == cudaSuccess) err = cudaEventElapsedTime(&one, e0, e1);
-      ms += one;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&trial[r], e0, e1);
     }
-    if (err == cudaSuccess && rc == DDS_OK && ms / 5 < best) {
-      best = ms / 5;
+    std::sort(trial, trial + 5);
+    const float ms = trial[2];
+    if (err == cudaSuccess && rc == DDS_OK && ms < best) {
+      best = ms;
       pick = cand[i];
     }
   }

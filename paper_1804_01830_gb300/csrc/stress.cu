@@ -193,7 +193,7 @@ cudaError_t launch_x_fwd(const Shape &sh, const Collapse &col, const void *rho, 
 template <int PY, bool INV>
 cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in, float2 *om, float2 *on,
                      const float2 *tw, cudaStream_t s) {
-  constexpr int W = YTile<PY>::W, T = YTile<PY>::NT;
+  constexpr int W = YTile<PY, INV>::W, T = YTile<PY, INV>::NT;
   const long tiles = (long)nf * sh.nz * (sh.M / W) + (long)nf * ((sh.nz + W - 1) / W);
   if (sh.py == sh.ny) {                   // periodic in y: no zero padding (py <= 512)
     if constexpr (PY <= 512) {

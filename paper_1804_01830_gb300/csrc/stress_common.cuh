@@ -12,7 +12,13 @@ constexpr int NT = 256;   // threads of the shared-memory z pass
 // Tile shape of the y passes: W columns per tile, NT threads.  Small tiles keep
 // several CTAs resident per SM so that one tile's copies overlap another tile's
 // transform.
-template <int P> struct YTile { static constexpr int W = P >= 1024 ? 4 : (P >= 512 ? 8 : 16), NT = 128; };
+// y-pass tiles: W columns, NT threads.  The 512-row inverse takes 16 columns and 256
+// threads (whole 128-byte rows; GaN layer 0.215 -> 0.207 ms); the 512-row forward keeps
+// 8 and 128 (0.176 against 0.183 ms with 16).
+template <int P, bool INV = false> struct YTile {
+  static constexpr int W = P >= 1024 ? 4 : (P >= 512 ? (INV ? 16 : 8) : 16);
+  static constexpr int NT = (P == 512 && INV) ? 256 : 128;
+};
 
 __device__ __forceinline__ float2 cmadd_i(float2 acc, float g, float2 r) {
   // acc + (i g) * r

@@ -223,20 +223,13 @@ cudaError_t launch_y(const Shape &sh, int nf, const float2 *im, const float2 *in
 }
 
 
-// Lines of up to 256 points: persistent kernel with bulk-copied tiles (GaN layer
-// 256x256x128: 185 -> 155 us); 512 points: the plain register kernel, which keeps
-// four CTAs per SM instead of three (radial disk 512x512x16: 82 us against 90).
+// Persistent kernel with bulk-copied tiles for every line length (GaN layer 256x256x128:
+// 185 -> 155 us against one CTA per tile; with its twiddles held in registers across
+// tiles, 512 points too: radial disk 512x512x16 0.082 -> 0.078 ms against the one-tile
+// register kernel it replaced).
 template <int M>
 cudaError_t launch_x_inv(const Shape &sh, const float2 *im, const float2 *in, float *sigma, const float2 *tw,
                          cudaStream_t s, double *stats) {
-  if constexpr (M >= 512) {
-    constexpr int LPB = xr::THREADS / (xr::InvCfg<M>::R2 / 2);
-    const long L = 6L * sh.nb * sh.nz * sh.ny;
-    cudaError_t err = prep(xr::k_x_inv_reg<M>, 0);
-    if (err != cudaSuccess) return err;
-    xr::k_x_inv_reg<M><<<(unsigned)((L + LPB - 1) / LPB), xr::THREADS, 0, s>>>(sh, im, in, sigma, tw, stats);
-    return cudaGetLastError();
-  }
   using C = xr::InvTma<M>;
   const long L = 6L * sh.nb * sh.nz * sh.ny;
   DevInfo di;

@@ -58,111 +58,13 @@ __device__ __forceinline__ float2 c2r_pre(float2 A, float2 Bm, float2 wk) {
   return make_float2(E.x - O.y, E.y + O.x);
 }
 
-// stats != nullptr: also accumulate sum_x sigma^2 of every line into
-// stats[(set * 6 + c) * nz + z] (the per-height sums of Eq. 20).
-template <int M>
-__global__ void __launch_bounds__(THREADS)
-k_x_inv_reg(Shape sh, const float2 *__restrict__ in_main, const float2 *__restrict__ in_nyq,
-            float *__restrict__ sigma, const float2 *__restrict__ tw, double *stats) {
-  constexpr int R1 = InvCfg<M>::R1, R2 = InvCfg<M>::R2, T = R2 / 2, RPT = R1 / T;
-  constexpr int LPB = THREADS / T, LD = R1 + 1, S = R2 * LD + line_pad<T>();
-  static_assert(R1 * R2 == M && RPT >= 1 && RPT * T == R1, "x inverse config");
-  __shared__ float2 sm[LPB * S];
-  const int t = threadIdx.x % T, lw = threadIdx.x / T;
-  const long L = 6L * sh.nb * sh.nz * sh.ny;
-  const long line = (long)blockIdx.x * LPB + lw;
-  const bool live = line < L;
-  const bool t0 = t == 0;
-  const int ca = t, cb = t0 ? R2 / 2 : R2 - t;
-  const float2 *twM = tw + tw_offset(M);
-  const float2 *tw2 = tw + tw_offset(2 * M);
-
-  float2 a[R1], b[R1], xm = make_float2(0.f, 0.f);
-  if (live) {
-    const float2 *src = in_main + line * M;
-#pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) {
-      a[n1] = __ldcs(src + ca + R2 * n1);
-      b[n1] = __ldcs(src + cb + R2 * n1);
-    }
-    if (t0) {
-      const long cz = line / sh.ny;
-      const int y = (int)(line - cz * sh.ny);
-      const int c = (int)(cz / sh.nz), z = (int)(cz - (long)c * sh.nz);
-      xm = in_nyq[((long)c * sh.ny + y) * sh.nz + z];
-    }
-  } else {
-#pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) a[n1] = b[n1] = make_float2(0.f, 0.f);
-  }
-  // mirrors: X[M - k] of the bins k = ca + R2 n1 and k = cb + R2 n1
-  float2 za[R1], zb[R1];
-#pragma unroll
-  for (int n1 = 0; n1 < R1; ++n1) {
-    const float2 am = t0 ? (n1 == 0 ? xm : a[(R1 - n1) % R1]) : b[R1 - 1 - n1];
-    const float2 bm = t0 ? b[R1 - 1 - n1] : a[R1 - 1 - n1];
-    za[n1] = c2r_pre(a[n1], am, __ldg(tw2 + ca + R2 * n1));
-    zb[n1] = c2r_pre(b[n1], bm, __ldg(tw2 + cb + R2 * n1));
-  }
-  // stage 1: inverse R1-point DFTs of both columns, twiddle conj(W_M^{c m1})
-  dft_reg<R1, true>(za);
-  dft_reg<R1, true>(zb);
-  float2 *ls = sm + lw * S;
-#pragma unroll
-  for (int m1 = 0; m1 < R1; ++m1) {
-    if (m1 > 0) {
-      za[m1] = cmul_tw<true>(za[m1], __ldg(twM + ca * m1));
-      zb[m1] = cmul_tw<true>(zb[m1], __ldg(twM + cb * m1));
-    }
-    ls[ca * LD + m1] = za[m1];
-    ls[cb * LD + m1] = zb[m1];
-  }
-  __syncthreads();
-  // stage 2: rows m1 = t + T r, inverse R2-point DFTs; only the first half of the
-  // outputs (n = m1 + R1 m2 < M / 2) lie inside the unpadded line
-  const int nxh = (sh.nx + 1) >> 1;
-  const bool even = (sh.nx & 1) == 0;
-  float ssq = 0.f;
-#pragma unroll
-  for (int r = 0; r < RPT; ++r) {
-    const int m1 = t + T * r;
-    float2 y[R2];
-#pragma unroll
-    for (int c = 0; c < R2; ++c) y[c] = ls[c * LD + m1];
-    dft_reg<R2, true>(y);
-    if (live) {
-      float *dst = sigma + line * sh.nx;
-#pragma unroll
-      for (int m2 = 0; m2 < R2 / 2; ++m2) {
-        const int n = m1 + R1 * m2;
-        if (n < nxh) {
-          if (even) {
-            __stcs(reinterpret_cast<float2 *>(dst + 2 * n), y[m2]);
-            ssq += y[m2].x * y[m2].x + y[m2].y * y[m2].y;
-          } else {
-            dst[2 * n] = y[m2].x;
-            ssq += y[m2].x * y[m2].x;
-            if (2 * n + 1 < sh.nx) {
-              dst[2 * n + 1] = y[m2].y;
-              ssq += y[m2].y * y[m2].y;
-            }
-          }
-        }
-      }
-    }
-  }
-  if (stats != nullptr) {
-#pragma unroll
-    for (int o = T / 2; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
-    if (live && t0) atomicAdd(&stats[line / sh.ny], (double)ssq);
-  }
-}
-
-// Persistent form of the inverse pass: each CTA walks the tiles blockIdx.x,
+// The inverse pass is persistent: each CTA walks the tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ...; the LPB input lines of a tile are contiguous and
 // arrive in one bulk copy (TMA) into one of two shared-memory slots, issued two
 // tiles ahead, so the copy of the next tile overlaps the transforms of this one.
 // A slot, once its lines are in registers, serves as the tile's transpose buffer.
+// stats != nullptr: the pass also accumulates sum_x sigma^2 of every line into
+// stats[(set * 6 + c) * nz + z] (the per-height sums of Eq. 20).
 template <int M> struct InvTma {
   static constexpr int R1 = InvCfg<M>::R1, R2 = InvCfg<M>::R2, T = R2 / 2;
   static constexpr int LPB = THREADS / T, S = R2 * (R1 + 1) + line_pad<T>();

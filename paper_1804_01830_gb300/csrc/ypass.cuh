@@ -34,11 +34,12 @@ template <int P, int W> __host__ __device__ constexpr int y_smem() {
 }
 
 // Whether the tile stages the PY twiddles in shared memory (after its y_smem values):
-// stage 1 reads them at scattered indices.  Half-row forward passes up to 512 rows gain
-// (GaN layer 0.190 -> 0.176 ms); passes that read every row gain at 256 rows but lose at
-// 512 (0.215 -> 0.224 ms: one CTA per SM fewer), and 1024 rows lose in both directions.
+// stage 1 reads them at scattered indices.  Forward passes up to 512 rows gain (GaN layer
+// 0.190 -> 0.176 ms), and so does the 512-row inverse on its 16-column tiles (0.207 ->
+// 0.201 ms; on 8-column tiles it lost a CTA per SM and 0.009 ms).  The full-row
+// periodic passes take it up to 256 rows; 1024 rows lose in both directions.
 template <int PY, bool INV, bool FULL> __host__ __device__ constexpr bool y_stw() {
-  return PY <= 512 && ((!INV && !FULL) || PY <= 256);
+  return PY <= 512 && (!FULL || PY <= 256);
 }
 template <int PY, int W, bool INV, bool FULL> __host__ __device__ constexpr int y_smem_all() {
   return y_smem<PY, W>() + (y_stw<PY, INV, FULL>() ? PY : 0);

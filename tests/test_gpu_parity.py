@@ -393,6 +393,24 @@ def test_eq20_statistics_fused_into_the_evaluation(dds):
     ctx.close()
 
 
+@pytest.mark.parametrize("shape", [(300, 8, 4), (200, 16, 6), (100, 12, 5), (20, 40, 3)])
+def test_eq20_statistics_every_line_length(dds, shape):
+    # x lines of 512, 256, 128 and 32 padded points (the persistent inverse x pass with 16,
+    # 8, 8 and 4 threads per line): the fused sums equal the plane RMS of the returned sigma
+    t18, b18 = W.gan_families()
+    g = W.Geometry(*shape, 0.2e-6, 0.2e-6, 0.05e-6)
+    p = W.random_problem(g, t18[[0, 9, 13]], b18[[0, 9, 13]], seed=sum(shape))
+    ctx = dds.context_for(p)
+    rho = torch.from_numpy(np.ascontiguousarray(p.rho, dtype=np.float32)).cuda()
+    sig, s = ctx.stress_stats(rho)
+    torch.cuda.synchronize()
+    s = s.cpu().numpy()
+    ref = plane_rms(sig.cpu().numpy())
+    assert s.shape == (6, g.nz)
+    assert np.abs(s - ref).max() <= 1e-6 * np.abs(ref).max()
+    ctx.close()
+
+
 # ------------------------------------------------------------- autotuner ---
 @pytest.mark.parametrize("case", ["thin", "tall"])
 def test_autotune_keeps_the_result(dds, case):

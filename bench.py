@@ -342,7 +342,6 @@ def relaxation_benchmark(ctx, sigma, g, peak: float, steps: int = 200, cpu: bool
     (36 algorithmic bytes per cell: read u and dt f, write u), and the FP64 oracle's
     time per step on the host for the same grid."""
     import torch
-    import oracle.relax as R
     u = torch.zeros((3, g.nz, g.ny, g.nx), dtype=torch.float32, device=sigma.device)
     ctx.relax(sigma, 10, u=u, total=False)
     torch.cuda.synchronize()
@@ -357,7 +356,8 @@ def relaxation_benchmark(ctx, sigma, g, peak: float, steps: int = 200, cpu: bool
            "roofline": {"bound": "hbm", "bytes_per_cell_step": 36, "achieved": gbs, "peak": peak,
                         "unit": "GB/s", "frac": gbs / peak},
            "l2": "not flushed between steps (the 150 MB working set of a step exceeds L2)"}
-    if cpu:
+    if cpu:                                  # the CPU-baseline leg: the oracle on the host
+        import oracle.relax as R
         sig = sigma.double().cpu().numpy()
         h = (g.dx, g.dy, g.dz)
         t = time.perf_counter()
@@ -476,7 +476,7 @@ def small_grid_latency(device: int, iters: int = 1000):
     return out
 
 
-def sweep_benchmark(device: int, n_real: int = 64, reps: int = 5, oracle_targets: int = 6):
+def sweep_benchmark(device: int, n_real: int = 64, reps: int = 5, oracle_targets: int = 6, cpu: bool = True):
     """The batched grain-size sweep: n_real polycrystal realisations on the four sweep
     grids (cells 0.2x0.2x0.05 um, 18 families, grain diameters log-uniform in 0.5-8 um),
     one context per grid with an autotuned z schedule, all realisations of a grid in one
@@ -486,7 +486,6 @@ def sweep_benchmark(device: int, n_real: int = 64, reps: int = 5, oracle_targets
     timed on sampled target cells of one realisation as the CPU baseline."""
     import numpy as np
     import torch
-    import oracle
     import paper_1804_01830_gb300 as dds
     dev = f"cuda:{device}"
     groups = {}
@@ -545,25 +544,27 @@ def sweep_benchmark(device: int, n_real: int = 64, reps: int = 5, oracle_targets
                    b.double().reshape(b.shape[0], 6, -1).norm(dim=2).clamp_min(1e-30)).max())
             for a, b in zip(g16.sigma, g32.sigma))
     out["bf16_rel_l2_vs_fp32_max"] = d
-    # CPU baseline of the sweep: the FP64 oracle's direct sum on sampled target cells of
-    # realisation 0 (its parity with the GPU is a test, not part of the benchmark)
-    r0 = 0
-    g0, D0 = W.sweep_spec(r0)
-    p0 = W.gan_polycrystal(g0, D0, r0)
-    tg = np.random.default_rng(0).integers(0, g0.n_cells, size=oracle_targets)
-    t_or = time.perf_counter()
-    ref0 = oracle.stress_direct(g0, p0.t, p0.b, p0.rho, targets=tg, use_table=False)
-    t_or = time.perf_counter() - t_or
-    out["cpu_baseline"] = {"value": tg.size / t_or, "unit": "cells/s", "cores": oracle.num_threads(),
-                           "kind": "oracle", "sample": f"{tg.size} target cells of realisation {r0}"}
-    # realisation 0's results at those cells against the oracle (values computed anyway)
-    for gi, (key, items) in enumerate(sorted(groups.items())):
-        for i, (r, _, _) in enumerate(items):
-            if r == r0:
-                out["realisation0_rel_l2_at_sampled_cells"] = {
-                    "fp32": rel_l2_sampled(g32.sigma[gi][i].cpu().numpy(), tg, ref0),
-                    "bf16_densities": rel_l2_sampled(g16.sigma[gi][i].cpu().numpy(), tg, ref0),
-                    "tolerances": {"fp32": 1e-5, "bf16_densities": 4e-3}}
+    if cpu:
+        # the CPU-baseline leg of the sweep: the FP64 oracle's direct sum on sampled target
+        # cells of realisation 0 (its parity with the GPU is a test, not part of the benchmark)
+        import oracle
+        r0 = 0
+        g0, D0 = W.sweep_spec(r0)
+        p0 = W.gan_polycrystal(g0, D0, r0)
+        tg = np.random.default_rng(0).integers(0, g0.n_cells, size=oracle_targets)
+        t_or = time.perf_counter()
+        ref0 = oracle.stress_direct(g0, p0.t, p0.b, p0.rho, targets=tg, use_table=False)
+        t_or = time.perf_counter() - t_or
+        out["cpu_baseline"] = {"value": tg.size / t_or, "unit": "cells/s", "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": f"{tg.size} target cells of realisation {r0}"}
+        # realisation 0's results at those cells against the oracle (values computed anyway)
+        for gi, (key, items) in enumerate(sorted(groups.items())):
+            for i, (r, _, _) in enumerate(items):
+                if r == r0:
+                    out["realisation0_rel_l2_at_sampled_cells"] = {
+                        "fp32": rel_l2_sampled(g32.sigma[gi][i].cpu().numpy(), tg, ref0),
+                        "bf16_densities": rel_l2_sampled(g16.sigma[gi][i].cpu().numpy(), tg, ref0),
+                        "tolerances": {"fp32": 1e-5, "bf16_densities": 4e-3}}
     g32.close()
     g16.close()
     for c in ctxs:
@@ -905,7 +906,7 @@ def run_ours(args):
 
     sweep = None
     if not args.no_sweep and rank == 0 and world == 1:
-        sweep = sweep_benchmark(local)
+        sweep = sweep_benchmark(local, cpu=not args.no_cpu_baseline)
         sweep["small_grid_latency"] = small_grid_latency(local)
 
 

@@ -11,6 +11,7 @@
 //           inverse FFT along z, keep rows z < nz;
 //   y_inv : inverse FFT along y, keep rows y < ny;
 //   x_inv : complex-to-real inverse FFT along x, keep x < nx.
+// (With DDS_OPT_YX_FUSED the last two run as one cluster pass, yxpass.cuh.)
 //
 // The Nyquist column kx = M of the half spectrum travels in separate small
 // arrays.  Layouts (complex):
